@@ -1,0 +1,340 @@
+"""Benchmark of the PMACE hot path on GB300: patch-updates/s.
+
+A step is one PMACE iteration (Algorithm 1) over every window of the
+workload: the fused agent sweep (steps S0-S5) and the consensus gather (S6),
+two kernel launches.  The default workload is a 600 x 600 complex object,
+a 256 x 256 probe and an 18 x 18 jittered raster (324 windows) with FP32
+amplitudes at Poisson peak 1e5, drawn by the seeded generator (synthetic
+stand-in for the paper's LANL image and probe, which are not available).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line is printed by rank 0.  Under torchrun every rank runs an
+independent replica of the job on its own GPU (no data-path collective;
+"scaling": "weak"); the time is the maximum over ranks.  `--impl reference`
+times the FP64 CPU oracle instead (rank 0 only), on a bounded sample of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PMACE patch-updates/s"
+UNIT = "patch-updates/s"
+ALPHA, RHO, KAPPA = 0.5, 0.5, 1.25
+WORKLOAD = ("p256: object 600x600 complex64, probe 256x256 (Gaussian sigma 48 px, random quadratic "
+            "phase), 18x18 raster step 20 px +-2 px jitter = 324 windows, FP32 amplitudes, "
+            "Poisson peak 1e5, alpha 0.5, rho 0.5, kappa 1.25")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "agent_p256_traffic.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2111_14240_gb300", "csrc", f)
+                  for f in ("agent.cuh", "fft_smem.cuh", "pmace_internal.h")]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def agent_bytes_per_patch(np_: int, amp_bytes: int = 4) -> int:
+    """Algorithmic HBM bytes of the agent sweep per window: read q, read y,
+    write u, write q (complex64 = 8 B, amplitude 4 or 2 B per pixel).  The
+    window of the consensus image it reads is L2-resident and not counted."""
+    return np_ * np_ * (8 + amp_bytes + 8 + 8)
+
+
+def iteration_bytes(np_: int, J: int, n1: int, n2: int, amp_bytes: int = 4) -> int:
+    """Algorithmic bytes of one whole iteration: the agent sweep plus the
+    gather's read of u and its image traffic (write xbar, read Lambda^-1)."""
+    return J * (agent_bytes_per_patch(np_, amp_bytes) + np_ * np_ * 8) + n1 * n2 * (8 + 4)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+        return dist, world, rank, local
+    return None, 1, 0, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def stored_traffic():
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    with open(TRAFFIC_FILE) as f:
+        d = json.load(f)
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    return float(d["bytes_per_launch"])
+
+
+# --------------------------------------------------------------------- oracle
+def oracle_rate(w, seconds: float, max_windows: int | None = None):
+    """FP64 oracle on a sub-scan of the workload: Algorithm 1 over the first
+    m windows (m sized so one iteration takes about `seconds`).  Returns
+    (patch-updates/s, m, iterations timed, seconds)."""
+    from oracle import pmace_oracle as orc
+    probe, offs, y = w.probe, w.offsets, w.y
+    # estimate the per-window cost on a few windows
+    m0 = min(8, len(offs))
+    t0 = time.perf_counter()
+    orc.pmace(y[:m0], probe, offs[:m0], w.x.shape, alpha=ALPHA, rho=RHO, kappa=KAPPA, n_iter=1)
+    per = (time.perf_counter() - t0) / m0
+    m = max(1, min(len(offs), int(seconds / max(per, 1e-6))))
+    if max_windows:
+        m = min(m, max_windows)
+    t0 = time.perf_counter()
+    orc.pmace(y[:m], probe, offs[:m], w.x.shape, alpha=ALPHA, rho=RHO, kappa=KAPPA, n_iter=1)
+    dt = time.perf_counter() - t0
+    return m / dt, m, dt
+
+
+def run_reference(args):
+    dist, world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    from paper_2111_14240_gb300 import datagen
+    w = datagen.make_workload("p256", seed=1)
+    J = w.J
+    budget = 150.0
+    per_step = max(0.2, min(6.0, budget / max(1, args.steps + args.warmup)))
+    from oracle import pmace_oracle as orc
+    probe, offs, y = w.probe, w.offsets, w.y
+    m0 = 8
+    t0 = time.perf_counter()
+    orc.pmace(y[:m0], probe, offs[:m0], w.x.shape, alpha=ALPHA, rho=RHO, kappa=KAPPA, n_iter=1)
+    per = (time.perf_counter() - t0) / m0
+    m = max(1, min(J, int(per_step / per)))
+    sub = (y[:m], probe, offs[:m], w.x.shape)
+    v = None
+    for _ in range(args.warmup):
+        v = orc.pmace(*sub, alpha=ALPHA, rho=RHO, kappa=KAPPA, n_iter=1, v0=v)["v"]
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v = orc.pmace(*sub, alpha=ALPHA, rho=RHO, kappa=KAPPA, n_iter=1, v0=v)["v"]
+    dt = time.perf_counter() - t0
+    val = m * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"Algorithm 1 (FP64 numpy, single thread) over the first {m} of "
+                                   f"{J} windows per step; each step one iteration"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    dist, world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_2111_14240_gb300 import datagen
+    from paper_2111_14240_gb300 import pmace as pm
+
+    w = datagen.make_workload("p256", seed=1)
+    J, np_ = w.J, w.np_
+    n1, n2 = w.x.shape
+    probe32 = np.ascontiguousarray(w.probe.astype(np.complex64))
+    y32 = np.ascontiguousarray(w.y.astype(np.float32))
+    stream = torch.cuda.current_stream()
+
+    rec = pm.Reconstruction(probe32, w.offsets, y32, (n1, n2), kappa=KAPPA, stream=stream)
+    plan = rec.plan()
+    rec.iterate(args.warmup, ALPHA, RHO)
+    torch.cuda.synchronize()
+    pm.pmace_set_profiling(rec.h, True)
+    pm.pmace_kernel_times(rec.h, reset=True)
+
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        start.record(stream)
+        rec.iterate(args.steps, ALPHA, RHO)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = start.elapsed_time(stop)
+    kt = pm.pmace_kernel_times(rec.h, reset=True)
+    pm.pmace_set_profiling(rec.h, False)
+    r_fp, r_data = rec.residual()
+    rec.close()
+
+    # end to end through the C ABI from pinned host buffers: create (H2D of
+    # probe, offsets, amplitudes), K iterations, residual and image (D2H)
+    y_pin = torch.from_numpy(y32).pin_memory()
+    p_pin = torch.view_as_real(torch.from_numpy(probe32)).contiguous().pin_memory()
+    img_pin = torch.empty((n1, n2, 2), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    h = pm.pmace_create(n1, n2, np_, J, KAPPA, p_pin, w.offsets, y_pin, pm.PMACE_AMP_F32,
+                        inputs_on_device=False, stream=stream)
+    pm.pmace_iterate(h, args.steps, ALPHA, RHO, stream=stream)
+    pm.pmace_residual(h, stream=stream)
+    pm.pmace_get_image(h, img_pin, stream=stream)
+    e2e_s = time.perf_counter() - t0
+    pm.pmace_destroy(h)
+    h2d = y32.nbytes + probe32.nbytes + w.offsets.nbytes
+    d2h = img_pin.numel() * 4 + 16
+
+    if dist:
+        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_s = float(t[0]), float(t[1])
+    if rank != 0:
+        return 0
+
+    value = world * J * args.steps / (ms / 1e3)
+    peak, peak_kind = measured_peaks()
+    agent_avg_ms = kt["agent_ms"] / max(1, kt["agent_launches"])
+    cons_avg_ms = kt["consensus_ms"] / max(1, kt["consensus_launches"])
+    bytes_launch = J * agent_bytes_per_patch(np_)
+    achieved = bytes_launch / (agent_avg_ms / 1e3) / 1e9
+    it_bytes = iteration_bytes(np_, J, n1, n2)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "windows": J, "probe": np_, "image": [n1, n2],
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "no flush: per-step working set (q, u, y) is "
+                         f"{(J * np_ * np_ * 20) / 1e6:.0f} MB > 129 MB L2",
+                   "plan": plan},
+        "roofline": {"bound": "hbm", "kernel": "agent_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": stored_traffic(),
+                     "peak_kind": f"{peak_kind} (copy bandwidth)",
+                     "algorithmic_bytes_per_launch": bytes_launch,
+                     "avg_launch_ms": agent_avg_ms},
+        "kernels": {"agent_avg_ms": agent_avg_ms, "consensus_avg_ms": cons_avg_ms,
+                    "iteration_bytes": it_bytes,
+                    "iteration_GBps": it_bytes / (ms / args.steps / 1e3) / 1e9},
+        "residual": {"r_fp": r_fp, "r_data": r_data},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks.summary(),
+        "e2e": {"value": world * J * args.steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                "note": "one whole job through the C ABI from pinned host memory: create + K "
+                        "iterations + residual + image readback; bytes amortised over K"},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        rate, m, dt = oracle_rate(w, seconds=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"one Algorithm 1 iteration (FP64 numpy, one thread) over "
+                                          f"the first {m} of {J} windows, {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,168 @@
+/*
+ * pmace.h -- C ABI of the GB300 PMACE hot path.
+ *
+ * PMACE (Projected Multi-Agent Consensus Equilibrium, Zhai, Buzzard,
+ * Wohlberg, Bouman, arXiv 2111.14240) reconstructs a complex transmittance
+ * image x (N1 x N2) from far-field amplitudes y_j (Np x Np) measured at J
+ * probe positions, with a known complex probe d (Np x Np) (Section II,
+ * forward model z_j = Pois(|F D P_j x|^2), y_j = sqrt(z_j)).  One iteration
+ * of Algorithm 1 applies the J probe-weighted proximal agents F_j (Section
+ * III-A, equation F-interpolate), the probe-weighted consensus G (equation
+ * xjbar) and the Mann step v <- v + 2 rho (z - w).
+ *
+ * Conventions shared by every call:
+ *  - complex arrays are interleaved float32 (re, im), row-major, C order;
+ *  - F is the 2-D orthonormal DFT with the DC term at index [0][0] and no
+ *    fftshift, so y_j must be given in that layout;
+ *  - a `stream` argument is a cudaStream_t passed as void* (NULL = the
+ *    legacy default stream); calls are asynchronous on it unless stated;
+ *  - the library copies every input it keeps; callers keep ownership of
+ *    their buffers and may free them once the call has returned (host
+ *    buffers) or once the stream has passed the call (device buffers);
+ *  - no call aborts the process; every failure is reported as a status and
+ *    the message is available from pmace_last_error().  A status other than
+ *    PMACE_OK leaves the handle valid unless documented otherwise.
+ *  - the library runs on the CUDA device that is current when pmace_create
+ *    is called; later calls on the handle must be made with that device
+ *    current.
+ */
+#ifndef PMACE_H
+#define PMACE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pmace_job* pmace_handle;
+
+typedef enum {
+    PMACE_OK = 0,
+    PMACE_ERR_INVALID_ARG = 1,      /* bad pointer, size, offset or amplitude value */
+    PMACE_ERR_OOM = 2,              /* device or host allocation failed */
+    PMACE_ERR_CUDA = 3,             /* a CUDA runtime call failed */
+    PMACE_ERR_UNSUPPORTED_SIZE = 4, /* Np not in {32, 64, 128, 256} */
+    PMACE_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up */
+    PMACE_ERR_STATE = 6             /* call not valid in the handle's current state */
+} pmace_status;
+
+typedef enum {
+    PMACE_AMP_F32 = 0,        /* amps: float32 [J][Np][Np] */
+    PMACE_AMP_F16_SCALED = 1  /* amps: IEEE binary16 codes [J][Np][Np]; y = code * scales[j] */
+} pmace_amp_format;
+
+/* Problem sizes (Section II): image N1 x N2 (n1 rows, n2 columns), probe and
+ * detector Np x Np, J probe positions; kappa is the probe exponent of the
+ * consensus weights |D|^kappa (equation xjbar); it is fixed at creation
+ * because the weight image Lambda = sum_j P_j^t |D|^kappa depends on it. */
+typedef struct {
+    int32_t n1, n2, np, J;
+    float kappa;
+} pmace_dims;
+
+/* Per-call iteration parameters: alpha >= 0 is the noise-to-signal ratio of
+ * the agents (equation F-interpolate), rho in (0, 1) the Mann averaging
+ * parameter (Algorithm 1). */
+typedef struct {
+    float alpha, rho;
+} pmace_step;
+
+/* Create a reconstruction job: copies the inputs to the device, builds the
+ * scan-overlap lists and the weight image Lambda, and sets Algorithm 1's
+ * initial stacks w = v = [P_j x^(0)]_j.
+ *   dims    : sizes and kappa; 1 <= Np <= min(n1, n2), J >= 1, kappa finite.
+ *   probe   : d, Np*Np complex (2*Np*Np floats).
+ *   offsets : J*2 int32, (row, col) of the top-left corner of window j; each
+ *             must satisfy 0 <= row <= n1-Np and 0 <= col <= n2-Np
+ *             (P_j extracts x[row:row+Np, col:col+Np]).
+ *   amps    : measured amplitudes y_j in the layout of `fmt`; values must be
+ *             finite and >= 0 (checked on the device; INVALID_ARG otherwise).
+ *   scales  : J float32 per-pattern scales for PMACE_AMP_F16_SCALED, else NULL.
+ *   init    : x^(0), n1*n2 complex, or NULL for the energy-matched constant
+ *             c = sqrt(sum_j ||y_j||^2 / (J ||d||^2)).
+ *   inputs_on_device : 0 = all array inputs are host pointers, 1 = probe,
+ *             amps, scales and init are device pointers (offsets and dims
+ *             are always host memory).
+ *   out     : receives the handle (NULL on failure).
+ * Synchronises `stream` once (input validation).  Returns
+ * UNSUPPORTED_SIZE for Np outside {32, 64, 128, 256}. */
+pmace_status pmace_create(const pmace_dims* dims, const float* probe, const int32_t* offsets,
+                          const void* amps, pmace_amp_format fmt, const float* scales,
+                          const float* init, int inputs_on_device, void* stream,
+                          pmace_handle* out);
+
+/* Run n >= 0 iterations of Algorithm 1 (w <- F(v); z <- G(2w - v);
+ * v <- v + 2 rho (z - w)) with the given alpha, rho.  Asynchronous; two
+ * kernel launches per iteration. */
+pmace_status pmace_iterate(pmace_handle h, int32_t n, const pmace_step* step, void* stream);
+
+/* Algorithm 1's output x_hat = Lambda^-1 sum_j P_j^t |D|^kappa v_j for the
+ * current v (pixels no window covers read 0).  out: n1*n2 complex, host
+ * (out_on_device = 0; the call then synchronises `stream`) or device memory. */
+pmace_status pmace_get_image(pmace_handle h, float* out, int out_on_device, void* stream);
+
+/* The current patch stack v (J*Np*Np complex), host or device memory. */
+pmace_status pmace_get_patches(pmace_handle h, float* out, int out_on_device, void* stream);
+
+/* Residuals of the last iteration, computed on the device in FP64 in a fixed
+ * order and returned in out[0..1]:
+ *   out[0] = ||z_prev - w|| / ||w||: disagreement between the previous
+ *            consensus stack and the new agent outputs (zero at the
+ *            Algorithm 1 fixed point; z_prev = v before the first iteration);
+ *   out[1] = sum_j ||y_j - |F D v_j| ||^2 / sum_j ||y_j||^2 at the agents'
+ *            inputs (the data term of equation eq1 up to 1/(2 sigma_n^2)).
+ * Synchronises `stream`.  STATE if no iteration has run yet. */
+pmace_status pmace_residual(pmace_handle h, double out[2], void* stream);
+
+/* Checkpoint.  The state is the pending stack q = v - 2 rho w (J*Np*Np
+ * complex), the consensus image xbar (n1*n2 complex), the iteration count
+ * and the pending rho; together they determine v = q + 2 rho P xbar.  Resuming
+ * from a saved state reproduces the uninterrupted run bit for bit. */
+typedef struct {
+    int64_t iterations;
+    float rho_pending;
+    int32_t reserved;
+} pmace_state_info;
+
+pmace_status pmace_get_state(pmace_handle h, float* q, float* xbar, pmace_state_info* info,
+                             int on_device, void* stream);
+pmace_status pmace_set_state(pmace_handle h, const float* q, const float* xbar,
+                             const pmace_state_info* info, int on_device, void* stream);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream around
+ * every agent and consensus launch while enabled.  pmace_kernel_times
+ * synchronises on the recorded events and returns the summed milliseconds
+ * and launch counts since the last reset (any pointer may be NULL). */
+pmace_status pmace_set_profiling(pmace_handle h, int enable);
+pmace_status pmace_kernel_times(pmace_handle h, double* agent_ms, int64_t* agent_launches,
+                                double* consensus_ms, int64_t* consensus_launches, int reset);
+
+/* Kernel plan chosen for this job: cluster size (CTAs per patch) and threads
+ * per CTA of the agent kernel, and the dynamic shared memory per CTA. */
+typedef struct {
+    int32_t cluster, threads, smem_bytes, tile_h, tile_w;
+} pmace_plan;
+pmace_status pmace_get_plan(pmace_handle h, pmace_plan* plan);
+
+/* Device bytes held by the job. */
+int64_t pmace_device_bytes(pmace_handle h);
+
+/* Release everything the job holds (NULL is a no-op).  Synchronises the
+ * device work of the handle first. */
+void pmace_destroy(pmace_handle h);
+
+/* Message of the last failure on h (or of the last failed pmace_create when
+ * h is NULL); never NULL, empty when there was none. */
+const char* pmace_last_error(pmace_handle h);
+
+const char* pmace_status_string(pmace_status s);
+
+/* ABI version, bumped on any incompatible change. */
+int32_t pmace_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMACE_H */

@@ -1,0 +1,16 @@
+// Agent sweep instantiations for 64 x 64 probes.
+#include "agent.cuh"
+
+namespace pmace {
+
+cudaError_t agent_entry_64(const AgentArgs* a, int cluster, int amp_f16, cudaStream_t s,
+                           AgentPlanInfo* info) {
+    switch (cluster) {
+        case 1: return agent_entry_impl<64, 1>(a, amp_f16, s, info);
+        case 2: return agent_entry_impl<64, 2>(a, amp_f16, s, info);
+        case 4: return agent_entry_impl<64, 4>(a, amp_f16, s, info);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pmace

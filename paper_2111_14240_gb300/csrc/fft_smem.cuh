@@ -1,0 +1,254 @@
+// Register butterflies and in-place shared-memory FFT stages for the agent
+// kernel.  The 2-D orthonormal DFT F of Section II is applied as a sequence
+// of in-place radix-r stages: decimation in frequency (DIF, butterfly then
+// twiddle) for the forward transform, which leaves the spectrum in
+// digit-reversed order, and decimation in time (DIT, conjugate twiddle then
+// inverse butterfly) in the reverse stage order for F^*, which takes the
+// digit-reversed spectrum back to natural order.  The magnitude replacement
+// between them is pointwise, so no reordering pass is ever needed; the
+// measured amplitudes are stored in the same digit-reversed order once, at
+// job creation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cooperative_groups.h>
+
+namespace pmace {
+
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 operator*(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+
+// cos(2 pi m / 16), sin(2 pi m / 16) for m = 0..15, as exact decimal values
+// of the mathematical constants (rounded to float at compile time).
+__host__ __device__ constexpr double k_cos16(int m) {
+    constexpr double c1 = 0.92387953251128675613, c2 = 0.70710678118654752440,
+                     c3 = 0.38268343236508977173;
+    constexpr double t[16] = {1.0, c1, c2, c3, 0.0, -c3, -c2, -c1,
+                              -1.0, -c1, -c2, -c3, 0.0, c3, c2, c1};
+    return t[m & 15];
+}
+__host__ __device__ constexpr double k_sin16(int m) { return k_cos16((m + 12) & 15); }
+
+// a * W_16^M with W_16 = exp(-2 pi i / 16) (forward) or exp(+2 pi i / 16)
+// (INV); trivial factors are applied without multiplications.
+template <int M, bool INV>
+__device__ __forceinline__ float2 twiddle16(float2 a) {
+    constexpr int m = M & 15;
+    if constexpr (m == 0) {
+        return a;
+    } else if constexpr (m == 8) {
+        return make_float2(-a.x, -a.y);
+    } else if constexpr ((m == 4 && !INV) || (m == 12 && INV)) {
+        return make_float2(a.y, -a.x);   // * (-i)
+    } else if constexpr ((m == 12 && !INV) || (m == 4 && INV)) {
+        return make_float2(-a.y, a.x);   // * (+i)
+    } else {
+        constexpr float c = (float)k_cos16(m);
+        constexpr float s = INV ? (float)k_sin16(m) : -(float)k_sin16(m);
+        return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+    }
+}
+
+// In-register DFT of length R (2, 4, 8, 16), natural order in and out:
+// X[k] = sum_j x[j] exp(-+2 pi i j k / R).
+template <int R, bool INV>
+struct Dft;
+
+template <bool INV>
+struct Dft<2, INV> {
+    __device__ __forceinline__ static void run(float2 (&x)[2]) {
+        float2 a = x[0];
+        x[0] = a + x[1];
+        x[1] = a - x[1];
+    }
+};
+
+template <bool INV>
+struct Dft<4, INV> {
+    __device__ __forceinline__ static void run(float2 (&x)[4]) {
+        float2 a = x[0] + x[2], b = x[0] - x[2], c = x[1] + x[3];
+        float2 d = twiddle16<4, INV>(x[1] - x[3]);
+        x[0] = a + c;
+        x[2] = a - c;
+        x[1] = b + d;
+        x[3] = b - d;
+    }
+};
+
+// Four-step split R = R1 * R2 with index maps j = R2*j1 + j2, k = k1 + R1*k2:
+// X[k1 + R1 k2] = sum_j2 W_R2^{j2 k2} W_R^{j2 k1} sum_j1 x[R2 j1 + j2] W_R1^{j1 k1}.
+template <int R1, int R2, bool INV>
+struct FourStep {
+    static constexpr int R = R1 * R2;
+    template <int J2>
+    __device__ __forceinline__ static void inner(const float2 (&x)[R], float2 (&t)[R]) {
+        float2 s[R1];
+#pragma unroll
+        for (int j1 = 0; j1 < R1; ++j1) s[j1] = x[R2 * j1 + J2];
+        Dft<R1, INV>::run(s);
+        apply_tw<J2, 0>(s, t);
+    }
+    template <int J2, int K1>
+    __device__ __forceinline__ static void apply_tw(const float2 (&s)[R1], float2 (&t)[R]) {
+        if constexpr (K1 < R1) {
+            t[J2 * R1 + K1] = twiddle16<(J2 * K1 * (16 / R)), INV>(s[K1]);
+            apply_tw<J2, K1 + 1>(s, t);
+        }
+    }
+    template <int J2>
+    __device__ __forceinline__ static void all_inner(const float2 (&x)[R], float2 (&t)[R]) {
+        if constexpr (J2 < R2) {
+            inner<J2>(x, t);
+            all_inner<J2 + 1>(x, t);
+        }
+    }
+    __device__ __forceinline__ static void run(float2 (&x)[R]) {
+        float2 t[R];
+        all_inner<0>(x, t);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            float2 s[R2];
+#pragma unroll
+            for (int j2 = 0; j2 < R2; ++j2) s[j2] = t[j2 * R1 + k1];
+            Dft<R2, INV>::run(s);
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) x[k1 + R1 * k2] = s[k2];
+        }
+    }
+};
+
+template <bool INV>
+struct Dft<8, INV> {
+    __device__ __forceinline__ static void run(float2 (&x)[8]) { FourStep<4, 2, INV>::run(x); }
+};
+
+template <bool INV>
+struct Dft<16, INV> {
+    __device__ __forceinline__ static void run(float2 (&x)[16]) { FourStep<4, 4, INV>::run(x); }
+};
+
+// Padded shared-memory column index: one float2 of padding after every 16,
+// which makes the stride-16 accesses of the short-span stages conflict free.
+__device__ __forceinline__ int pcol(int c) { return c + (c >> 4); }
+template <int N>
+struct TileGeom {
+    static constexpr int RS = N + N / 16;  // padded row stride in float2
+};
+
+// Forward twiddle W_N^m = exp(-2 pi i m / N) from a table tw[0..N).
+template <bool INV>
+__device__ __forceinline__ float2 apply_table_tw(float2 a, float2 w) {
+    return INV ? cmulc(a, w) : cmul(a, w);
+}
+
+// One in-place radix-R stage along the row axis (inside each row of the
+// tile), span L, for NROWS rows of length N.  DIF: butterfly then twiddle
+// W_L^{b k}; DIT (INV): conjugate twiddle then inverse butterfly.
+template <int N, int NROWS, int L, int R, bool INV, int T>
+__device__ __forceinline__ void row_stage(float2* __restrict__ tile, const float2* __restrict__ tw) {
+    constexpr int RS = TileGeom<N>::RS;
+    constexpr int S = L / R;
+    constexpr int BPR = N / R;
+    constexpr int NB = NROWS * BPR;
+    for (int t = threadIdx.x; t < NB; t += T) {
+        const int row = t / BPR, m = t % BPR;
+        const int b = m % S;
+        const int base = (m / S) * L + b;
+        float2* rp = tile + row * RS;
+        float2 x[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) x[k] = rp[pcol(base + k * S)];
+        if constexpr (INV) {
+            if constexpr (S > 1) {
+#pragma unroll
+                for (int k = 1; k < R; ++k) x[k] = cmulc(x[k], tw[b * k * (N / L)]);
+            }
+            Dft<R, true>::run(x);
+        } else {
+            Dft<R, false>::run(x);
+            if constexpr (S > 1) {
+#pragma unroll
+                for (int k = 1; k < R; ++k) x[k] = cmul(x[k], tw[b * k * (N / L)]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) rp[pcol(base + k * S)] = x[k];
+    }
+}
+
+// One in-place radix-R stage along the column axis inside the CTA's own
+// NROWS rows, span L <= NROWS, of a length-N column transform (twiddles from
+// the same length-N table).
+template <int N, int NROWS, int L, int R, bool INV, int T>
+__device__ __forceinline__ void col_stage(float2* __restrict__ tile, const float2* __restrict__ tw) {
+    constexpr int RS = TileGeom<N>::RS;
+    constexpr int S = L / R;
+    constexpr int NB = (NROWS / R) * N;
+    for (int t = threadIdx.x; t < NB; t += T) {
+        const int col = t % N, m = t / N;
+        const int b = m % S;
+        const int rbase = (m / S) * L + b;
+        float2* cp = tile + pcol(col);
+        float2 x[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) x[k] = cp[(rbase + k * S) * RS];
+        if constexpr (INV) {
+            if constexpr (S > 1) {
+#pragma unroll
+                for (int k = 1; k < R; ++k) x[k] = cmulc(x[k], tw[b * k * (N / L)]);
+            }
+            Dft<R, true>::run(x);
+        } else {
+            Dft<R, false>::run(x);
+            if constexpr (S > 1) {
+#pragma unroll
+                for (int k = 1; k < R; ++k) x[k] = cmul(x[k], tw[b * k * (N / L)]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) cp[(rbase + k * S) * RS] = x[k];
+    }
+}
+
+// The column-axis stage of span N and radix C across the C CTAs of a
+// cluster: CTA k holds global rows [k*NROWS, (k+1)*NROWS), so the butterfly
+// at local row b combines row b of every CTA.  Each CTA takes NROWS/C of the
+// butterflies, reading and writing the peers' tiles through distributed
+// shared memory; a butterfly's elements are read and written by one thread
+// only, so the stage is in place without staging.
+template <int N, int NROWS, int C, bool INV, int T>
+__device__ __forceinline__ void cross_stage(float2* const (&peer)[C], const float2* __restrict__ tw,
+                                            int rank) {
+    constexpr int RS = TileGeom<N>::RS;
+    constexpr int BR = NROWS / C;     // butterfly rows per CTA
+    constexpr int NB = BR * N;
+    for (int t = threadIdx.x; t < NB; t += T) {
+        const int col = t % N;
+        const int b = rank * BR + t / N;
+        const int off = b * RS + pcol(col);
+        float2 x[C];
+#pragma unroll
+        for (int k = 0; k < C; ++k) x[k] = peer[k][off];
+        if constexpr (INV) {
+#pragma unroll
+            for (int k = 1; k < C; ++k) x[k] = cmulc(x[k], tw[b * k]);
+            Dft<C, true>::run(x);
+        } else {
+            Dft<C, false>::run(x);
+#pragma unroll
+            for (int k = 1; k < C; ++k) x[k] = cmul(x[k], tw[b * k]);
+        }
+#pragma unroll
+        for (int k = 0; k < C; ++k) peer[k][off] = x[k];
+    }
+}
+
+}  // namespace pmace

@@ -1,0 +1,646 @@
+// Host runtime and C ABI of the PMACE hot path (declared in include/pmace.h).
+//
+// A job keeps its whole working set resident on one GPU:
+//   q     [J][Np][Np] complex64  pending Mann stack q = v - 2 rho w
+//   u     [J][Np][Np] complex64  agent reflection u = 2w - v (input of G)
+//   y     [J][Np][Np] f32 or f16 amplitudes, digit-reversed kernel order
+//   xbar  [n1][n2]    complex64  consensus image of the last iteration
+//   laminv[n1][n2]    f32        Lambda^-1 (0 where Lambda = 0)
+// plus the probe tables (d, 1/d, |d|^kappa, twiddles) and the scan-overlap
+// lists.  One iteration of Algorithm 1 is two launches: the fused agent
+// sweep (agent.cuh) and the pixel-owner consensus gather (support.cu).
+#include "../../include/pmace.h"
+#include "pmace_internal.h"
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace pmace;
+
+namespace {
+
+constexpr int kMaxCluster = 16;
+constexpr int kPrepBlocks = 608;
+
+thread_local std::string g_create_error;
+
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+
+}  // namespace
+
+struct pmace_job {
+    int device = 0;
+    pmace_dims dims{};
+    int amp_f16 = 0;
+    int cluster = 1;
+    AgentPlanInfo plan{};
+    int tiles_x = 0, tiles_y = 0, ntiles = 0;
+
+    float2 *q = nullptr, *u = nullptr, *xbar = nullptr, *probe = nullptr, *dinv = nullptr,
+           *tw = nullptr, *img_tmp = nullptr;
+    void* y = nullptr;
+    float *yscale = nullptr, *laminv = nullptr, *wk = nullptr;
+    int2* offs = nullptr;
+    int *tile_ptr = nullptr, *tile_list = nullptr, *err = nullptr;
+    double *partials = nullptr, *red_out = nullptr;
+    int64_t bytes = 0;
+
+    int64_t iterations = 0;
+    float rho_pending = 0.5f;
+
+    bool profiling = false;
+    std::vector<EventPair> ev_agent, ev_cons;
+    size_t n_agent = 0, n_cons = 0;
+
+    std::string error;
+};
+
+namespace {
+
+pmace_status fail(pmace_job* h, pmace_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->error = buf;
+    else g_create_error = buf;
+    return st;
+}
+
+pmace_status cuda_fail(pmace_job* h, cudaError_t e, const char* what) {
+    return fail(h, e == cudaErrorMemoryAllocation ? PMACE_ERR_OOM : PMACE_ERR_CUDA, "%s: %s (%s)",
+                what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define PM_CUDA(h, call)                                            \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);    \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(pmace_job* h, T** p, size_t count) {
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (e == cudaSuccess) h->bytes += (int64_t)bytes;
+    return e;
+}
+
+bool np_supported(int np) { return np == 32 || np == 64 || np == 128 || np == 256; }
+
+cudaError_t agent_entry(int np, const AgentArgs* a, int cluster, int amp, cudaStream_t s,
+                        AgentPlanInfo* info) {
+    switch (np) {
+        case 32: return agent_entry_32(a, cluster, amp, s, info);
+        case 64: return agent_entry_64(a, cluster, amp, s, info);
+        case 128: return agent_entry_128(a, cluster, amp, s, info);
+        case 256: return agent_entry_256(a, cluster, amp, s, info);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Default CTAs per patch for each probe size (the smallest cluster whose
+// tile leaves room for more than one resident CTA per SM).
+int default_cluster(int np) {
+    if (const char* env = std::getenv("PMACE_AGENT_CLUSTER")) {
+        const int c = std::atoi(env);
+        if (c > 0) return c;
+    }
+    return np == 256 ? 8 : np == 128 ? 2 : 1;
+}
+
+// Frequency index held at each position after in-place DIF stages with the
+// given radices (outer stage first): position k*(L/r) + p of a span-L block
+// holds frequency k + r * (frequency of p in the span-L/r sub-transform).
+void dif_order(const std::vector<int>& radices, size_t level, int L, std::vector<int>& out) {
+    if (L == 1) {
+        out.assign(1, 0);
+        return;
+    }
+    const int r = radices[level];
+    std::vector<int> sub;
+    dif_order(radices, level + 1, L / r, sub);
+    out.assign(L, 0);
+    for (int k = 0; k < r; ++k)
+        for (int p = 0; p < L / r; ++p) out[k * (L / r) + p] = k + r * sub[p];
+}
+
+std::vector<int> radices_of(int L) {
+    const RadixPlan p = radix_plan(L);
+    std::vector<int> v{p.first};
+    if (p.second > 1) v.push_back(p.second);
+    return v;
+}
+
+pmace_status build_tables(pmace_job* h, const std::vector<float>& probe_h,
+                          const std::vector<int32_t>& offs_h, cudaStream_t s,
+                          std::vector<std::vector<char>>& keep, int** perm_out) {
+    const int np = h->dims.np, J = h->dims.J;
+    const size_t P = (size_t)np * np;
+    // probe tables in double, rounded once
+    std::vector<float2> d(P), dinv(P), tw(np);
+    std::vector<float> wk(P);
+    double amax = 0.0;
+    for (size_t i = 0; i < P; ++i)
+        amax = std::max(amax, std::hypot((double)probe_h[2 * i], (double)probe_h[2 * i + 1]));
+    for (size_t i = 0; i < P; ++i) {
+        const double re = probe_h[2 * i], im = probe_h[2 * i + 1];
+        const double m = std::hypot(re, im);
+        d[i] = make_float2((float)re, (float)im);
+        wk[i] = (float)std::pow(m, (double)h->dims.kappa);
+        if (m > 1e-30 * amax && m > 0.0) {
+            const double m2 = re * re + im * im;
+            dinv[i] = make_float2((float)(re / m2), (float)(-im / m2));
+        } else {
+            dinv[i] = make_float2(0.f, 0.f);
+        }
+    }
+    for (int m = 0; m < np; ++m) {
+        const double ang = -2.0 * M_PI * (double)m / (double)np;
+        tw[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    // scan-overlap lists: for every gather tile the ascending list of windows that intersect it
+    const int TH = kGatherTileH, TW = kGatherTileW;
+    h->tiles_y = (h->dims.n1 + TH - 1) / TH;
+    h->tiles_x = (h->dims.n2 + TW - 1) / TW;
+    h->ntiles = h->tiles_x * h->tiles_y;
+    std::vector<int> cnt(h->ntiles + 1, 0);
+    auto tile_range = [&](int j, int& y0, int& y1, int& x0, int& x1) {
+        const int r = offs_h[2 * j], c = offs_h[2 * j + 1];
+        y0 = r / TH;
+        y1 = (r + np - 1) / TH;
+        x0 = c / TW;
+        x1 = (c + np - 1) / TW;
+    };
+    for (int j = 0; j < J; ++j) {
+        int y0, y1, x0, x1;
+        tile_range(j, y0, y1, x0, x1);
+        for (int ty = y0; ty <= y1; ++ty)
+            for (int tx = x0; tx <= x1; ++tx) cnt[ty * h->tiles_x + tx + 1]++;
+    }
+    for (int t = 0; t < h->ntiles; ++t) cnt[t + 1] += cnt[t];
+    std::vector<int> list(std::max(cnt[h->ntiles], 1));
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (int j = 0; j < J; ++j) {   // ascending j, so every list is ascending
+        int y0, y1, x0, x1;
+        tile_range(j, y0, y1, x0, x1);
+        for (int ty = y0; ty <= y1; ++ty)
+            for (int tx = x0; tx <= x1; ++tx) list[fill[ty * h->tiles_x + tx]++] = j;
+    }
+    // row and column spectra orders of the agent kernel
+    std::vector<int> rowperm, colperm;
+    dif_order(radices_of(np), 0, np, rowperm);
+    std::vector<int> crad;
+    if (h->cluster > 1) crad.push_back(h->cluster);
+    for (int r : radices_of(np / h->cluster)) crad.push_back(r);
+    dif_order(crad, 0, np, colperm);
+
+    PM_CUDA(h, dalloc(h, &h->probe, P));
+    PM_CUDA(h, dalloc(h, &h->dinv, P));
+    PM_CUDA(h, dalloc(h, &h->tw, (size_t)np));
+    PM_CUDA(h, dalloc(h, &h->wk, P));
+    PM_CUDA(h, dalloc(h, &h->offs, (size_t)J));
+    PM_CUDA(h, dalloc(h, &h->tile_ptr, (size_t)h->ntiles + 1));
+    PM_CUDA(h, dalloc(h, &h->tile_list, list.size()));
+    auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+        keep.emplace_back((const char*)src, (const char*)src + bytes);   // alive until the sync
+        return cudaMemcpyAsync(dst, keep.back().data(), bytes, cudaMemcpyHostToDevice, s);
+    };
+    PM_CUDA(h, up(h->probe, d.data(), P * sizeof(float2)));
+    PM_CUDA(h, up(h->dinv, dinv.data(), P * sizeof(float2)));
+    PM_CUDA(h, up(h->tw, tw.data(), np * sizeof(float2)));
+    PM_CUDA(h, up(h->wk, wk.data(), P * sizeof(float)));
+    PM_CUDA(h, up(h->offs, offs_h.data(), (size_t)J * 2 * sizeof(int32_t)));
+    PM_CUDA(h, up(h->tile_ptr, cnt.data(), cnt.size() * sizeof(int)));
+    PM_CUDA(h, up(h->tile_list, list.data(), list.size() * sizeof(int)));
+    // permutation tables (row order, then column order) live only until the amplitude pass
+    PM_CUDA(h, cudaMalloc(perm_out, 2 * np * sizeof(int)));
+    std::vector<int> both(rowperm);
+    both.insert(both.end(), colperm.begin(), colperm.end());
+    PM_CUDA(h, up(*perm_out, both.data(), both.size() * sizeof(int)));
+    return PMACE_OK;
+}
+
+GatherArgs gather_args(const pmace_job* h) {
+    GatherArgs g{};
+    g.wk = h->wk;
+    g.offs = h->offs;
+    g.tile_ptr = h->tile_ptr;
+    g.tile_list = h->tile_list;
+    g.laminv = h->laminv;
+    g.n1 = h->dims.n1;
+    g.n2 = h->dims.n2;
+    g.np = h->dims.np;
+    g.tiles_x = h->tiles_x;
+    return g;
+}
+
+void free_job(pmace_job* h) {
+    if (!h) return;
+    void* ptrs[] = {h->q, h->u, h->xbar, h->probe, h->dinv, h->tw, h->img_tmp, h->y, h->yscale,
+                    h->laminv, h->wk, h->offs, h->tile_ptr, h->tile_list, h->err, h->partials,
+                    h->red_out};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (auto* v : {&h->ev_agent, &h->ev_cons})
+        for (auto& e : *v) {
+            if (e.a) cudaEventDestroy(e.a);
+            if (e.b) cudaEventDestroy(e.b);
+        }
+    delete h;
+}
+
+cudaError_t record_pair(std::vector<EventPair>& pool, size_t& n, bool start, cudaStream_t s) {
+    if (start) {
+        if (n == pool.size()) {
+            EventPair p;
+            cudaError_t e = cudaEventCreate(&p.a);
+            if (e != cudaSuccess) return e;
+            e = cudaEventCreate(&p.b);
+            if (e != cudaSuccess) return e;
+            pool.push_back(p);
+        }
+        return cudaEventRecord(pool[n].a, s);
+    }
+    cudaError_t e = cudaEventRecord(pool[n].b, s);
+    ++n;
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t pmace_abi_version(void) { return 1; }
+
+const char* pmace_status_string(pmace_status s) {
+    switch (s) {
+        case PMACE_OK: return "ok";
+        case PMACE_ERR_INVALID_ARG: return "invalid argument";
+        case PMACE_ERR_OOM: return "out of memory";
+        case PMACE_ERR_CUDA: return "CUDA error";
+        case PMACE_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+        case PMACE_ERR_TIMEOUT: return "device wait timed out";
+        case PMACE_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char* pmace_last_error(pmace_handle h) {
+    return h ? h->error.c_str() : g_create_error.c_str();
+}
+
+pmace_status pmace_create(const pmace_dims* dims, const float* probe, const int32_t* offsets,
+                          const void* amps, pmace_amp_format fmt, const float* scales,
+                          const float* init, int inputs_on_device, void* stream,
+                          pmace_handle* out) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, PMACE_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!dims || !probe || !offsets || !amps)
+        return fail(nullptr, PMACE_ERR_INVALID_ARG, "dims, probe, offsets and amps are required");
+    const pmace_dims D = *dims;
+    if (D.n1 <= 0 || D.n2 <= 0 || D.np <= 0 || D.J <= 0)
+        return fail(nullptr, PMACE_ERR_INVALID_ARG, "sizes must be positive (n1=%d n2=%d np=%d J=%d)",
+                    D.n1, D.n2, D.np, D.J);
+    if (!np_supported(D.np))
+        return fail(nullptr, PMACE_ERR_UNSUPPORTED_SIZE, "np=%d not in {32, 64, 128, 256}", D.np);
+    if (D.np > D.n1 || D.np > D.n2)
+        return fail(nullptr, PMACE_ERR_INVALID_ARG, "np=%d exceeds the image %dx%d", D.np, D.n1, D.n2);
+    if (!std::isfinite(D.kappa))
+        return fail(nullptr, PMACE_ERR_INVALID_ARG, "kappa must be finite");
+    if (fmt != PMACE_AMP_F32 && fmt != PMACE_AMP_F16_SCALED)
+        return fail(nullptr, PMACE_ERR_INVALID_ARG, "unknown amplitude format %d", (int)fmt);
+    if (fmt == PMACE_AMP_F16_SCALED && !scales)
+        return fail(nullptr, PMACE_ERR_INVALID_ARG, "FP16 amplitudes need per-pattern scales");
+    if ((size_t)D.J * D.np * D.np > (size_t)INT32_MAX * 8)
+        return fail(nullptr, PMACE_ERR_INVALID_ARG, "stack too large");
+    for (int j = 0; j < D.J; ++j) {
+        const int r = offsets[2 * j], c = offsets[2 * j + 1];
+        if (r < 0 || c < 0 || r > D.n1 - D.np || c > D.n2 - D.np)
+            return fail(nullptr, PMACE_ERR_INVALID_ARG,
+                        "offset %d = (%d, %d) outside [0, %d] x [0, %d]", j, r, c, D.n1 - D.np,
+                        D.n2 - D.np);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int np = D.np, J = D.J;
+    const size_t P = (size_t)np * np, JP = (size_t)J * P, NI = (size_t)D.n1 * D.n2;
+
+    pmace_job* h = new (std::nothrow) pmace_job();
+    if (!h) return fail(nullptr, PMACE_ERR_OOM, "host allocation failed");
+    h->dims = D;
+    h->amp_f16 = fmt == PMACE_AMP_F16_SCALED;
+    cudaGetDevice(&h->device);
+
+    auto bail = [&](pmace_status st) {
+        g_create_error = h->error;
+        free_job(h);
+        return st;
+    };
+
+    // plan: requested cluster if it exists and fits, else the next smaller one
+    int c = std::min(default_cluster(np), kMaxCluster);
+    for (; c >= 1; c >>= 1) {
+        AgentPlanInfo info{};
+        if (agent_entry(np, nullptr, c, 0, s, &info) == cudaSuccess && info.launchable) {
+            h->plan = info;
+            break;
+        }
+        cudaGetLastError();
+    }
+    if (c < 1) return bail(fail(h, PMACE_ERR_UNSUPPORTED_SIZE, "no launchable agent plan for np=%d", np));
+    h->cluster = c;
+
+    // host copies of the small inputs
+    std::vector<float> probe_h(2 * P);
+    std::vector<int32_t> offs_h(offsets, offsets + 2 * (size_t)J);
+    if (inputs_on_device) {
+        cudaError_t e = cudaMemcpy(probe_h.data(), probe, 2 * P * sizeof(float), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return bail(cuda_fail(h, e, "probe copy"));
+    } else {
+        std::memcpy(probe_h.data(), probe, 2 * P * sizeof(float));
+    }
+    for (float v : probe_h)
+        if (!std::isfinite(v)) return bail(fail(h, PMACE_ERR_INVALID_ARG, "probe has non-finite values"));
+
+    std::vector<std::vector<char>> keep;
+    keep.reserve(16);
+    int* perm_d = nullptr;
+    auto bail_perm = [&](pmace_status st2) {
+        cudaStreamSynchronize(s);
+        if (perm_d) cudaFree(perm_d);
+        return bail(st2);
+    };
+    pmace_status st = build_tables(h, probe_h, offs_h, s, keep, &perm_d);
+    if (st != PMACE_OK) return bail_perm(st);
+
+    cudaError_t e;
+#define PM_CREATE(call)                                                    \
+    do {                                                                   \
+        e = (call);                                                        \
+        if (e != cudaSuccess) return bail_perm(cuda_fail(h, e, #call));   \
+    } while (0)
+    PM_CREATE(dalloc(h, &h->q, JP));
+    PM_CREATE(dalloc(h, &h->u, JP));
+    PM_CREATE(dalloc(h, &h->xbar, NI));
+    PM_CREATE(dalloc(h, &h->laminv, NI));
+    PM_CREATE(dalloc(h, &h->partials, (size_t)J * kMaxCluster * 4 + kPrepBlocks));
+    PM_CREATE(dalloc(h, &h->red_out, (size_t)4));
+    PM_CREATE(dalloc(h, &h->err, (size_t)1));
+    PM_CREATE(cudaMemsetAsync(h->err, 0, sizeof(int), s));
+    const size_t ybytes = JP * (h->amp_f16 ? sizeof(__half) : sizeof(float));
+    PM_CREATE(cudaMalloc(&h->y, std::max<size_t>(ybytes, 16)));
+    h->bytes += (int64_t)ybytes;
+
+    // amplitudes to kernel order (staged through u when they come from the host)
+    const void* amps_dev = amps;
+    if (!inputs_on_device) {
+        PM_CREATE(cudaMemcpyAsync(h->u, amps, ybytes, cudaMemcpyHostToDevice, s));
+        amps_dev = h->u;
+    }
+    if (h->amp_f16) {
+        PM_CREATE(dalloc(h, &h->yscale, (size_t)J));
+        PM_CREATE(cudaMemcpyAsync(h->yscale, scales, J * sizeof(float),
+                                  inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    }
+    double* sum_partials = h->partials + (size_t)J * kMaxCluster * 4;
+    PM_CREATE(launch_prep_amps(amps_dev, h->amp_f16, h->yscale, h->y, perm_d, perm_d + np, J, np,
+                               sum_partials, h->err, kPrepBlocks, s));
+    PM_CREATE(launch_reduce_partials(sum_partials, kPrepBlocks, 1, h->red_out, s));
+
+    // weight image Lambda^-1
+    GatherArgs g = gather_args(h);
+    g.lam_out = h->laminv;
+    PM_CREATE(launch_gather_weights(g, h->ntiles, s));
+
+    // initial stacks
+    double sumsq = 0.0;
+    PM_CREATE(cudaMemcpyAsync(&sumsq, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PM_CREATE(cudaStreamSynchronize(s));
+    int errflag = 0;
+    PM_CREATE(cudaMemcpy(&errflag, h->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (errflag & 1) return bail_perm(fail(h, PMACE_ERR_INVALID_ARG, "amplitudes must be finite and >= 0"));
+    double dsq = 0.0;
+    for (size_t i = 0; i < 2 * P; ++i) dsq += (double)probe_h[i] * probe_h[i];
+    const float cval = (dsq > 0.0) ? (float)std::sqrt(sumsq / ((double)J * dsq)) : 0.f;
+    const float2* init_dev = nullptr;
+    if (init) {
+        if (inputs_on_device) {
+            init_dev = reinterpret_cast<const float2*>(init);
+        } else {
+            PM_CREATE(cudaMemcpyAsync(h->xbar, init, NI * sizeof(float2), cudaMemcpyHostToDevice, s));
+            init_dev = h->xbar;
+        }
+        PM_CREATE(launch_check_finite(reinterpret_cast<const float*>(init_dev), (int64_t)NI * 2, h->err, s));
+    }
+    PM_CREATE(launch_init_stack(h->q, init_dev, make_float2(cval, 0.f), h->offs, J, np, D.n2, s));
+    PM_CREATE(cudaMemsetAsync(h->xbar, 0, NI * sizeof(float2), s));
+    PM_CREATE(cudaStreamSynchronize(s));
+    PM_CREATE(cudaMemcpy(&errflag, h->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (errflag & 2) return bail_perm(fail(h, PMACE_ERR_INVALID_ARG, "init has non-finite values"));
+#undef PM_CREATE
+    cudaFree(perm_d);
+    h->iterations = 0;
+    h->rho_pending = 0.5f;
+    *out = h;
+    return PMACE_OK;
+}
+
+pmace_status pmace_iterate(pmace_handle h, int32_t n, const pmace_step* step, void* stream) {
+    if (!h) return fail(nullptr, PMACE_ERR_INVALID_ARG, "NULL handle");
+    if (!step || n < 0) return fail(h, PMACE_ERR_INVALID_ARG, "step must be non-NULL and n >= 0");
+    const float alpha = step->alpha, rho = step->rho;
+    if (!(alpha >= 0.f) || !std::isfinite(alpha))
+        return fail(h, PMACE_ERR_INVALID_ARG, "alpha must be finite and >= 0 (got %g)", alpha);
+    if (!(rho > 0.f && rho < 1.f)) return fail(h, PMACE_ERR_INVALID_ARG, "rho must be in (0, 1) (got %g)", rho);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    AgentArgs a{};
+    a.q = h->q;
+    a.u = h->u;
+    a.xbar = h->xbar;
+    a.y = h->y;
+    a.yscale = h->yscale;
+    a.probe = h->probe;
+    a.dinv = h->dinv;
+    a.tw = h->tw;
+    a.offs = h->offs;
+    a.partials = h->partials;
+    a.n2 = h->dims.n2;
+    a.J = h->dims.J;
+    a.alpha = alpha;
+    a.rho_cur = rho;
+    GatherArgs g = gather_args(h);
+    g.src = h->u;
+    g.out = h->xbar;
+    for (int32_t it = 0; it < n; ++it) {
+        a.rho_prev = h->rho_pending;
+        a.first = h->iterations == 0 ? 1 : 0;
+        if (h->profiling) PM_CUDA(h, record_pair(h->ev_agent, h->n_agent, true, s));
+        PM_CUDA(h, agent_entry(h->dims.np, &a, h->cluster, h->amp_f16, s, nullptr));
+        if (h->profiling) {
+            PM_CUDA(h, record_pair(h->ev_agent, h->n_agent, false, s));
+            PM_CUDA(h, record_pair(h->ev_cons, h->n_cons, true, s));
+        }
+        PM_CUDA(h, launch_gather_consensus(g, h->ntiles, s));
+        if (h->profiling) PM_CUDA(h, record_pair(h->ev_cons, h->n_cons, false, s));
+        h->rho_pending = rho;
+        h->iterations++;
+    }
+    return PMACE_OK;
+}
+
+pmace_status pmace_get_image(pmace_handle h, float* out, int out_on_device, void* stream) {
+    if (!h) return fail(nullptr, PMACE_ERR_INVALID_ARG, "NULL handle");
+    if (!out) return fail(h, PMACE_ERR_INVALID_ARG, "out is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t NI = (size_t)h->dims.n1 * h->dims.n2;
+    float2* dst = reinterpret_cast<float2*>(out);
+    if (!out_on_device) {
+        if (!h->img_tmp) PM_CUDA(h, dalloc(h, &h->img_tmp, NI));
+        dst = h->img_tmp;
+    }
+    GatherArgs g = gather_args(h);
+    g.src = h->q;
+    g.xbar_in = h->xbar;
+    g.out = dst;
+    g.two_rho = 2.0f * h->rho_pending;
+    PM_CUDA(h, launch_gather_readout(g, h->ntiles, s));
+    if (!out_on_device) {
+        PM_CUDA(h, cudaMemcpyAsync(out, dst, NI * sizeof(float2), cudaMemcpyDeviceToHost, s));
+        PM_CUDA(h, cudaStreamSynchronize(s));
+    }
+    return PMACE_OK;
+}
+
+pmace_status pmace_get_patches(pmace_handle h, float* out, int out_on_device, void* stream) {
+    if (!h) return fail(nullptr, PMACE_ERR_INVALID_ARG, "NULL handle");
+    if (!out) return fail(h, PMACE_ERR_INVALID_ARG, "out is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t JP = (size_t)h->dims.J * h->dims.np * h->dims.np;
+    // u is dead between iterations (G consumed it), so it serves as staging
+    float2* dst = out_on_device ? reinterpret_cast<float2*>(out) : h->u;
+    PM_CUDA(h, launch_patches_from_state(h->q, h->xbar, h->offs, dst, h->dims.J, h->dims.np,
+                                         h->dims.n2, 2.0f * h->rho_pending, s));
+    if (!out_on_device) {
+        PM_CUDA(h, cudaMemcpyAsync(out, dst, JP * sizeof(float2), cudaMemcpyDeviceToHost, s));
+        PM_CUDA(h, cudaStreamSynchronize(s));
+    }
+    return PMACE_OK;
+}
+
+pmace_status pmace_residual(pmace_handle h, double out[2], void* stream) {
+    if (!h) return fail(nullptr, PMACE_ERR_INVALID_ARG, "NULL handle");
+    if (!out) return fail(h, PMACE_ERR_INVALID_ARG, "out is NULL");
+    if (h->iterations == 0) return fail(h, PMACE_ERR_STATE, "no iteration has run yet");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double r[4] = {0, 0, 0, 0};
+    PM_CUDA(h, launch_reduce_partials(h->partials, h->dims.J * h->cluster, 4, h->red_out, s));
+    PM_CUDA(h, cudaMemcpyAsync(r, h->red_out, sizeof(r), cudaMemcpyDeviceToHost, s));
+    PM_CUDA(h, cudaStreamSynchronize(s));
+    out[0] = r[1] > 0 ? std::sqrt(r[0] / r[1]) : 0.0;
+    out[1] = r[3] > 0 ? r[2] / r[3] : 0.0;
+    return PMACE_OK;
+}
+
+pmace_status pmace_get_state(pmace_handle h, float* q, float* xbar, pmace_state_info* info,
+                             int on_device, void* stream) {
+    if (!h) return fail(nullptr, PMACE_ERR_INVALID_ARG, "NULL handle");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t JP = (size_t)h->dims.J * h->dims.np * h->dims.np, NI = (size_t)h->dims.n1 * h->dims.n2;
+    if (q) PM_CUDA(h, cudaMemcpyAsync(q, h->q, JP * sizeof(float2), k, s));
+    if (xbar) PM_CUDA(h, cudaMemcpyAsync(xbar, h->xbar, NI * sizeof(float2), k, s));
+    if (info) {
+        info->iterations = h->iterations;
+        info->rho_pending = h->rho_pending;
+        info->reserved = 0;
+    }
+    if (!on_device) PM_CUDA(h, cudaStreamSynchronize(s));
+    return PMACE_OK;
+}
+
+pmace_status pmace_set_state(pmace_handle h, const float* q, const float* xbar,
+                             const pmace_state_info* info, int on_device, void* stream) {
+    if (!h) return fail(nullptr, PMACE_ERR_INVALID_ARG, "NULL handle");
+    if (!q || !xbar || !info) return fail(h, PMACE_ERR_INVALID_ARG, "q, xbar and info are required");
+    if (info->iterations < 0 || !(info->rho_pending > 0.f && info->rho_pending < 1.f))
+        return fail(h, PMACE_ERR_INVALID_ARG, "invalid state info");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t JP = (size_t)h->dims.J * h->dims.np * h->dims.np, NI = (size_t)h->dims.n1 * h->dims.n2;
+    PM_CUDA(h, cudaMemcpyAsync(h->q, q, JP * sizeof(float2), k, s));
+    PM_CUDA(h, cudaMemcpyAsync(h->xbar, xbar, NI * sizeof(float2), k, s));
+    if (!on_device) PM_CUDA(h, cudaStreamSynchronize(s));
+    h->iterations = info->iterations;
+    h->rho_pending = info->rho_pending;
+    return PMACE_OK;
+}
+
+pmace_status pmace_set_profiling(pmace_handle h, int enable) {
+    if (!h) return fail(nullptr, PMACE_ERR_INVALID_ARG, "NULL handle");
+    h->profiling = enable != 0;
+    return PMACE_OK;
+}
+
+pmace_status pmace_kernel_times(pmace_handle h, double* agent_ms, int64_t* agent_launches,
+                                double* consensus_ms, int64_t* consensus_launches, int reset) {
+    if (!h) return fail(nullptr, PMACE_ERR_INVALID_ARG, "NULL handle");
+    double ta = 0.0, tc = 0.0;
+    for (size_t i = 0; i < h->n_agent; ++i) {
+        float ms = 0.f;
+        PM_CUDA(h, cudaEventSynchronize(h->ev_agent[i].b));
+        PM_CUDA(h, cudaEventElapsedTime(&ms, h->ev_agent[i].a, h->ev_agent[i].b));
+        ta += ms;
+    }
+    for (size_t i = 0; i < h->n_cons; ++i) {
+        float ms = 0.f;
+        PM_CUDA(h, cudaEventSynchronize(h->ev_cons[i].b));
+        PM_CUDA(h, cudaEventElapsedTime(&ms, h->ev_cons[i].a, h->ev_cons[i].b));
+        tc += ms;
+    }
+    if (agent_ms) *agent_ms = ta;
+    if (agent_launches) *agent_launches = (int64_t)h->n_agent;
+    if (consensus_ms) *consensus_ms = tc;
+    if (consensus_launches) *consensus_launches = (int64_t)h->n_cons;
+    if (reset) h->n_agent = h->n_cons = 0;
+    return PMACE_OK;
+}
+
+pmace_status pmace_get_plan(pmace_handle h, pmace_plan* plan) {
+    if (!h) return fail(nullptr, PMACE_ERR_INVALID_ARG, "NULL handle");
+    if (!plan) return fail(h, PMACE_ERR_INVALID_ARG, "plan is NULL");
+    plan->cluster = h->cluster;
+    plan->threads = h->plan.threads;
+    plan->smem_bytes = h->plan.smem_bytes;
+    plan->tile_h = kGatherTileH;
+    plan->tile_w = kGatherTileW;
+    return PMACE_OK;
+}
+
+int64_t pmace_device_bytes(pmace_handle h) { return h ? h->bytes : 0; }
+
+void pmace_destroy(pmace_handle h) {
+    if (!h) return;
+    int cur = 0;
+    const int dev = h->device;
+    cudaGetDevice(&cur);
+    if (cur != dev) cudaSetDevice(dev);
+    cudaDeviceSynchronize();
+    free_job(h);
+    if (cur != dev) cudaSetDevice(cur);
+}
+
+}  // extern "C"

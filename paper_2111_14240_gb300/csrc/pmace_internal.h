@@ -1,0 +1,93 @@
+// Internal interfaces between the host runtime (pmace_api.cu) and the CUDA
+// kernels.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pmace {
+
+// Radix plan of a length-L transform: at most two in-place stages,
+// radices (first, second); second == 1 means a single stage.
+struct RadixPlan {
+    int first, second;
+};
+__host__ __device__ constexpr RadixPlan radix_plan(int L) {
+    return L == 256 ? RadixPlan{16, 16}
+         : L == 128 ? RadixPlan{16, 8}
+         : L == 64  ? RadixPlan{8, 8}
+         : L == 32  ? RadixPlan{8, 4}
+         : L == 16  ? RadixPlan{16, 1}
+         : L == 8   ? RadixPlan{8, 1}
+                    : RadixPlan{0, 0};
+}
+
+// Arguments of one agent sweep (steps S0-S5 of one iteration, all patches).
+struct AgentArgs {
+    float2* q;              // [J][Np][Np] pending stack q = v - 2 rho w (read, then overwritten)
+    float2* u;              // [J][Np][Np] written: u = 2w - v
+    const float2* xbar;     // [n1][n2] consensus image of the previous iteration
+    const void* y;          // [J][Np][Np] amplitudes in kernel (digit-reversed) order
+    const float* yscale;    // [J] per-pattern scale (FP16 codes only)
+    const float2* probe;    // [Np][Np] d
+    const float2* dinv;     // [Np][Np] 1/d, (0,0) where d is treated as absent
+    const float2* tw;       // [Np] W_Np^m = exp(-2 pi i m / Np)
+    const int2* offs;       // [J] (row, col) window corners
+    double* partials;       // [J * cluster][4] residual partial sums
+    int n2;                 // image row stride (columns)
+    int J;
+    float alpha, rho_prev, rho_cur;
+    int first;              // 1 on the first iteration of the job
+};
+
+// Arguments of the pixel-owner gathers (weight image, consensus, readout).
+struct GatherArgs {
+    const float2* src;      // [J][Np][Np] stack to average (u or q)
+    const float* wk;        // [Np][Np] |d|^kappa
+    const int2* offs;       // [J]
+    const int* tile_ptr;    // [ntiles + 1] CSR row pointers
+    const int* tile_list;   // patch indices per tile, ascending
+    const float* laminv;    // [n1][n2] Lambda^-1 (0 where Lambda = 0)
+    const float2* xbar_in;  // readout: consensus image
+    float2* out;            // [n1][n2]
+    float* lam_out;         // weight-image mode: Lambda^-1 written here
+    int n1, n2, np, tiles_x;
+    float two_rho;          // readout: 2 rho
+};
+
+constexpr int kGatherTileH = 32;
+constexpr int kGatherTileW = 32;
+constexpr int kGatherThreads = 256;
+
+// Geometry of one agent plan (probe size, CTAs per patch).
+struct AgentPlanInfo {
+    int threads;      // threads per CTA
+    int smem_bytes;   // dynamic shared memory per CTA
+    int launchable;   // the device can co-schedule at least one cluster
+};
+
+// Agent entry points, one per probe size (each in its own translation unit).
+// With a == nullptr they only fill `info` (cudaErrorInvalidValue if the
+// (np, cluster) pair has no instantiation); otherwise they launch the sweep.
+cudaError_t agent_entry_32(const AgentArgs* a, int cluster, int amp_f16, cudaStream_t s, AgentPlanInfo* info);
+cudaError_t agent_entry_64(const AgentArgs* a, int cluster, int amp_f16, cudaStream_t s, AgentPlanInfo* info);
+cudaError_t agent_entry_128(const AgentArgs* a, int cluster, int amp_f16, cudaStream_t s, AgentPlanInfo* info);
+cudaError_t agent_entry_256(const AgentArgs* a, int cluster, int amp_f16, cudaStream_t s, AgentPlanInfo* info);
+
+// Support kernels (support.cu).
+cudaError_t launch_gather_weights(const GatherArgs& g, int ntiles, cudaStream_t s);
+cudaError_t launch_gather_consensus(const GatherArgs& g, int ntiles, cudaStream_t s);
+cudaError_t launch_gather_readout(const GatherArgs& g, int ntiles, cudaStream_t s);
+cudaError_t launch_prep_amps(const void* amps_in, int amp_f16, const float* scales, void* y_out,
+                             const int* rowperm, const int* colperm, int J, int np,
+                             double* sumsq_partials, int* err_flag, int nblocks, cudaStream_t s);
+cudaError_t launch_reduce_partials(const double* partials, int nrows, int ncols, double* out,
+                                   cudaStream_t s);
+cudaError_t launch_init_stack(float2* q, const float2* init, float2 cval, const int2* offs,
+                              int J, int np, int n2, cudaStream_t s);
+cudaError_t launch_patches_from_state(const float2* q, const float2* xbar, const int2* offs,
+                                      float2* v, int J, int np, int n2, float two_rho,
+                                      cudaStream_t s);
+cudaError_t launch_check_finite(const float* data, int64_t n, int* err_flag, cudaStream_t s);
+
+}  // namespace pmace

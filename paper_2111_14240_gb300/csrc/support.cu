@@ -1,0 +1,249 @@
+// Support kernels of the PMACE hot path: the pixel-owner consensus gather
+// (step S6, equation xjbar), the weight image Lambda, the Algorithm 1
+// readout, the amplitude layout pass, the deterministic FP64 reduction of the
+// residual partials, and the stack initialisation of Algorithm 1.
+#include "pmace_internal.h"
+
+#include <cuda_fp16.h>
+
+namespace pmace {
+
+// ---------------------------------------------------------------------------
+// Pixel-owner gather over the scan-overlap lists.  One CTA owns a
+// kGatherTileH x kGatherTileW block of image pixels and walks the ascending
+// list of windows that intersect it; every pixel sums
+// |d(p - o_i)|^kappa * src_i(p - o_i) over the windows i that contain it in
+// ascending i, so the result is deterministic and needs no atomics.
+//   MODE 0: Lambda = sum_i |d|^kappa (FP64), writes Lambda^-1 (0 where Lambda = 0)
+//   MODE 1: xbar = Lambda^-1 sum_i P_i^t |D|^kappa u_i                 (G, S6)
+//   MODE 2: x_hat = Lambda^-1 sum_i P_i^t |D|^kappa q_i + 2 rho xbar   (readout)
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(kGatherThreads) gather_kernel(const GatherArgs g) {
+    constexpr int TH = kGatherTileH, TW = kGatherTileW;
+    constexpr int RPT = TH / (kGatherThreads / TW);   // rows per thread
+    const int tile = blockIdx.x;
+    const int ty0 = (tile / g.tiles_x) * TH, tx0 = (tile % g.tiles_x) * TW;
+    const int lane = threadIdx.x % TW, grp = threadIdx.x / TW;
+    const int px = tx0 + lane;
+    const int np = g.np;
+    const size_t P = (size_t)np * np;
+
+    using Acc = typename std::conditional<MODE == 0, double, float2>::type;
+    Acc acc[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        if constexpr (MODE == 0) acc[r] = 0.0;
+        else acc[r] = make_float2(0.f, 0.f);
+    }
+    const int lb = g.tile_ptr[tile], le = g.tile_ptr[tile + 1];
+    for (int li = lb; li < le; ++li) {
+        const int i = __ldg(g.tile_list + li);
+        const int2 o = __ldg(g.offs + i);
+        const int lx = px - o.y;
+        const bool inx = (unsigned)lx < (unsigned)np;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int py = ty0 + grp + r * (kGatherThreads / TW);
+            const int ly = py - o.x;
+            if (inx && (unsigned)ly < (unsigned)np) {
+                const int e = ly * np + lx;
+                const float wgt = __ldg(g.wk + e);
+                if constexpr (MODE == 0) {
+                    acc[r] += (double)wgt;
+                } else {
+                    const float2 s = __ldg(g.src + (size_t)i * P + e);
+                    acc[r].x = fmaf(wgt, s.x, acc[r].x);
+                    acc[r].y = fmaf(wgt, s.y, acc[r].y);
+                }
+            }
+        }
+    }
+    if (px >= g.n2) return;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        const int py = ty0 + grp + r * (kGatherThreads / TW);
+        if (py >= g.n1) continue;
+        const size_t p = (size_t)py * g.n2 + px;
+        if constexpr (MODE == 0) {
+            g.lam_out[p] = acc[r] > 0.0 ? (float)(1.0 / acc[r]) : 0.f;
+        } else {
+            const float li = __ldg(g.laminv + p);
+            float2 v = make_float2(acc[r].x * li, acc[r].y * li);
+            if constexpr (MODE == 2) {
+                const float2 xb = __ldg(g.xbar_in + p);
+                v.x = fmaf(g.two_rho, xb.x, v.x);
+                v.y = fmaf(g.two_rho, xb.y, v.y);
+            }
+            g.out[p] = v;
+        }
+    }
+}
+
+template <int MODE>
+static cudaError_t launch_gather(const GatherArgs& g, int ntiles, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    gather_kernel<MODE><<<ntiles, kGatherThreads, 0, s>>>(g);
+    return cudaGetLastError();
+}
+cudaError_t launch_gather_weights(const GatherArgs& g, int n, cudaStream_t s) { return launch_gather<0>(g, n, s); }
+cudaError_t launch_gather_consensus(const GatherArgs& g, int n, cudaStream_t s) { return launch_gather<1>(g, n, s); }
+cudaError_t launch_gather_readout(const GatherArgs& g, int n, cudaStream_t s) { return launch_gather<2>(g, n, s); }
+
+// ---------------------------------------------------------------------------
+// Amplitudes to kernel order: y_k[j][r][c] = y[j][colperm[r]][rowperm[c]]
+// (the digit-reversed order the in-place DIF stages leave the spectrum in),
+// validating finiteness and sign, and FP64 partial sums of y^2 per block.
+// ---------------------------------------------------------------------------
+constexpr int kPrepThreads = 256;
+
+template <int F16>
+__global__ void __launch_bounds__(kPrepThreads)
+prep_amps_kernel(const void* __restrict__ in, const float* __restrict__ scales, void* __restrict__ out,
+                 const int* __restrict__ rowperm, const int* __restrict__ colperm, int J, int np,
+                 double* __restrict__ partials, int* __restrict__ err) {
+    const size_t P = (size_t)np * np;
+    const size_t total = (size_t)J * P;
+    double s = 0.0;
+    int bad = 0;
+    for (size_t idx = (size_t)blockIdx.x * kPrepThreads + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * kPrepThreads) {
+        const size_t j = idx / P;
+        const int e = (int)(idx % P);
+        const int r = e / np, c = e % np;
+        const size_t src = j * P + (size_t)colperm[r] * np + rowperm[c];
+        float v;
+        if constexpr (F16) {
+            const __half h = static_cast<const __half*>(in)[src];
+            const float sc = scales[j];
+            const float hv = __half2float(h);
+            if (!(hv >= 0.f) || !(sc >= 0.f) || isinf(hv) || isinf(sc)) bad = 1;
+            static_cast<__half*>(out)[idx] = h;
+            v = hv * sc;
+        } else {
+            v = static_cast<const float*>(in)[src];
+            if (!(v >= 0.f) || isinf(v)) bad = 1;
+            static_cast<float*>(out)[idx] = v;
+        }
+        s += (double)v * (double)v;
+    }
+    if (bad) atomicOr(err, 1);
+    __shared__ double red[kPrepThreads];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kPrepThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+cudaError_t launch_prep_amps(const void* amps_in, int amp_f16, const float* scales, void* y_out,
+                             const int* rowperm, const int* colperm, int J, int np,
+                             double* partials, int* err, int nblocks, cudaStream_t s) {
+    if (amp_f16)
+        prep_amps_kernel<1><<<nblocks, kPrepThreads, 0, s>>>(amps_in, scales, y_out, rowperm, colperm,
+                                                            J, np, partials, err);
+    else
+        prep_amps_kernel<0><<<nblocks, kPrepThreads, 0, s>>>(amps_in, scales, y_out, rowperm, colperm,
+                                                            J, np, partials, err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-order FP64 reduction of an [nrows][ncols] table of partial sums
+// (ncols <= 4): out[c] = sum_r partials[r][c].  One CTA; each thread sums a
+// strided subset in order, then a fixed tree.  Deterministic run to run.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+reduce_partials_kernel(const double* __restrict__ p, int nrows, int ncols, double* __restrict__ out) {
+    __shared__ double red[256][4];
+    double s[4] = {0, 0, 0, 0};
+    for (int r = threadIdx.x; r < nrows; r += 256) {
+        for (int c = 0; c < ncols; ++c) s[c] += p[(size_t)r * ncols + c];
+    }
+    for (int c = 0; c < 4; ++c) red[threadIdx.x][c] = s[c];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            for (int c = 0; c < 4; ++c) red[threadIdx.x][c] += red[threadIdx.x + o][c];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < ncols) out[threadIdx.x] = red[0][threadIdx.x];
+}
+
+cudaError_t launch_reduce_partials(const double* partials, int nrows, int ncols, double* out,
+                                   cudaStream_t s) {
+    reduce_partials_kernel<<<1, 256, 0, s>>>(partials, nrows, ncols, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 initialisation w = v = [P_j x^(0)]_j, stored as the pending
+// stack q (the consensus image starts at 0, so v = q + 2 rho P xbar = q).
+// init == NULL means the constant image cval.
+// ---------------------------------------------------------------------------
+__global__ void init_stack_kernel(float2* __restrict__ q, const float2* __restrict__ init, float2 cval,
+                                  const int2* __restrict__ offs, int J, int np, int n2) {
+    const size_t P = (size_t)np * np;
+    const size_t total = (size_t)J * P;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        if (init == nullptr) {
+            q[idx] = cval;
+        } else {
+            const size_t j = idx / P;
+            const int e = (int)(idx % P);
+            const int2 o = offs[j];
+            q[idx] = init[(size_t)(o.x + e / np) * n2 + (o.y + e % np)];
+        }
+    }
+}
+
+cudaError_t launch_init_stack(float2* q, const float2* init, float2 cval, const int2* offs, int J,
+                              int np, int n2, cudaStream_t s) {
+    init_stack_kernel<<<1216, 256, 0, s>>>(q, init, cval, offs, J, np, n2);
+    return cudaGetLastError();
+}
+
+// v = q + 2 rho P_j xbar, the current Algorithm 1 stack.
+__global__ void patches_kernel(const float2* __restrict__ q, const float2* __restrict__ xbar,
+                               const int2* __restrict__ offs, float2* __restrict__ v, int J, int np,
+                               int n2, float two_rho) {
+    const size_t P = (size_t)np * np;
+    const size_t total = (size_t)J * P;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t j = idx / P;
+        const int e = (int)(idx % P);
+        const int2 o = offs[j];
+        const float2 xb = xbar[(size_t)(o.x + e / np) * n2 + (o.y + e % np)];
+        const float2 qv = q[idx];
+        v[idx] = make_float2(fmaf(two_rho, xb.x, qv.x), fmaf(two_rho, xb.y, qv.y));
+    }
+}
+
+cudaError_t launch_patches_from_state(const float2* q, const float2* xbar, const int2* offs,
+                                      float2* v, int J, int np, int n2, float two_rho,
+                                      cudaStream_t s) {
+    patches_kernel<<<1216, 256, 0, s>>>(q, xbar, offs, v, J, np, n2, two_rho);
+    return cudaGetLastError();
+}
+
+__global__ void check_finite_kernel(const float* __restrict__ d, int64_t n, int* __restrict__ err) {
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (!isfinite(d[i])) bad = 1;
+    }
+    if (bad) atomicOr(err, 2);
+}
+
+cudaError_t launch_check_finite(const float* data, int64_t n, int* err, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    check_finite_kernel<<<304, 256, 0, s>>>(data, n, err);
+    return cudaGetLastError();
+}
+
+}  // namespace pmace

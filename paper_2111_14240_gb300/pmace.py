@@ -1,0 +1,288 @@
+"""Thin ctypes binding of libpmace.so (include/pmace.h).
+
+The functions keep the C names and only marshal arguments: array arguments
+may be torch tensors (host or CUDA; their data pointers are passed through)
+or numpy arrays (host).  Every step of the hot path runs in the library's
+CUDA kernels; if the library is missing this module raises at import.
+`Reconstruction` wraps a handle for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libpmace.so")
+
+PMACE_OK = 0
+PMACE_ERR_INVALID_ARG = 1
+PMACE_ERR_OOM = 2
+PMACE_ERR_CUDA = 3
+PMACE_ERR_UNSUPPORTED_SIZE = 4
+PMACE_ERR_TIMEOUT = 5
+PMACE_ERR_STATE = 6
+PMACE_AMP_F32 = 0
+PMACE_AMP_F16_SCALED = 1
+
+
+class pmace_dims(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int32), ("n2", ctypes.c_int32), ("np", ctypes.c_int32),
+                ("J", ctypes.c_int32), ("kappa", ctypes.c_float)]
+
+
+class pmace_step(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_float), ("rho", ctypes.c_float)]
+
+
+class pmace_state_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int64), ("rho_pending", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
+
+
+class pmace_plan(ctypes.Structure):
+    _fields_ = [("cluster", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+                ("tile_w", ctypes.c_int32)]
+
+
+EXPORTS = ["pmace_create", "pmace_iterate", "pmace_get_image", "pmace_get_patches",
+           "pmace_residual", "pmace_get_state", "pmace_set_state", "pmace_set_profiling",
+           "pmace_kernel_times", "pmace_get_plan", "pmace_device_bytes", "pmace_destroy",
+           "pmace_last_error", "pmace_status_string", "pmace_abi_version"]
+
+
+def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build it with `python -m paper_2111_14240_gb300.build` "
+            "(there is no CPU fallback for the PMACE hot path)")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    P = ctypes.POINTER
+    sig = {
+        "pmace_create": (i32, [P(pmace_dims), vp, vp, vp, i32, vp, vp, ctypes.c_int, vp, P(vp)]),
+        "pmace_iterate": (i32, [vp, i32, P(pmace_step), vp]),
+        "pmace_get_image": (i32, [vp, vp, ctypes.c_int, vp]),
+        "pmace_get_patches": (i32, [vp, vp, ctypes.c_int, vp]),
+        "pmace_residual": (i32, [vp, P(ctypes.c_double), vp]),
+        "pmace_get_state": (i32, [vp, vp, vp, P(pmace_state_info), ctypes.c_int, vp]),
+        "pmace_set_state": (i32, [vp, vp, vp, P(pmace_state_info), ctypes.c_int, vp]),
+        "pmace_set_profiling": (i32, [vp, ctypes.c_int]),
+        "pmace_kernel_times": (i32, [vp, P(ctypes.c_double), P(i64), P(ctypes.c_double), P(i64),
+                                     ctypes.c_int]),
+        "pmace_get_plan": (i32, [vp, P(pmace_plan)]),
+        "pmace_device_bytes": (i64, [vp]),
+        "pmace_destroy": (None, [vp]),
+        "pmace_last_error": (ctypes.c_char_p, [vp]),
+        "pmace_status_string": (ctypes.c_char_p, [i32]),
+        "pmace_abi_version": (i32, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+class PmaceError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_lib.pmace_status_string(status).decode()}: {msg}")
+        self.status = status
+
+
+def _check(status: int, handle=None):
+    if status != PMACE_OK:
+        raise PmaceError(status, _lib.pmace_last_error(handle).decode(errors="replace"))
+
+
+def _ptr(a):
+    """Data pointer of a torch tensor or numpy array (must be contiguous)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _on_device(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+# ----------------------------------------------------------------- C names
+def pmace_abi_version() -> int:
+    return _lib.pmace_abi_version()
+
+
+def pmace_create(n1, n2, np_, J, kappa, probe, offsets, amps, amp_format=PMACE_AMP_F32,
+                 scales=None, init=None, inputs_on_device=None, stream=None):
+    """probe: (np, np) complex64 as float32 pairs; offsets: (J, 2) int32 host;
+    amps: (J, np, np) float32 or float16 codes; returns the handle (c_void_p)."""
+    if inputs_on_device is None:
+        inputs_on_device = _on_device(amps)
+    offs = offsets.cpu().numpy() if hasattr(offsets, "cpu") else np.asarray(offsets)
+    offs = np.ascontiguousarray(offs, dtype=np.int32)
+    dims = pmace_dims(int(n1), int(n2), int(np_), int(J), float(kappa))
+    h = ctypes.c_void_p()
+    st = _lib.pmace_create(ctypes.byref(dims), _ptr(probe), _ptr(offs), _ptr(amps), int(amp_format),
+                           _ptr(scales), _ptr(init), int(bool(inputs_on_device)), _stream(stream),
+                           ctypes.byref(h))
+    _check(st, None)
+    return h
+
+
+def pmace_iterate(h, n, alpha, rho, stream=None):
+    step = pmace_step(float(alpha), float(rho))
+    _check(_lib.pmace_iterate(h, int(n), ctypes.byref(step), _stream(stream)), h)
+
+
+def pmace_get_image(h, out, stream=None):
+    _check(_lib.pmace_get_image(h, _ptr(out), int(_on_device(out)), _stream(stream)), h)
+
+
+def pmace_get_patches(h, out, stream=None):
+    _check(_lib.pmace_get_patches(h, _ptr(out), int(_on_device(out)), _stream(stream)), h)
+
+
+def pmace_residual(h, stream=None):
+    out = (ctypes.c_double * 2)()
+    _check(_lib.pmace_residual(h, out, _stream(stream)), h)
+    return float(out[0]), float(out[1])
+
+
+def pmace_get_state(h, q, xbar, stream=None):
+    info = pmace_state_info()
+    on_dev = int(_on_device(q))
+    _check(_lib.pmace_get_state(h, _ptr(q), _ptr(xbar), ctypes.byref(info), on_dev, _stream(stream)), h)
+    return info
+
+
+def pmace_set_state(h, q, xbar, info, stream=None):
+    on_dev = int(_on_device(q))
+    _check(_lib.pmace_set_state(h, _ptr(q), _ptr(xbar), ctypes.byref(info), on_dev, _stream(stream)), h)
+
+
+def pmace_set_profiling(h, enable: bool):
+    _check(_lib.pmace_set_profiling(h, int(bool(enable))), h)
+
+
+def pmace_kernel_times(h, reset=False):
+    am, cm = ctypes.c_double(), ctypes.c_double()
+    an, cn = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.pmace_kernel_times(h, ctypes.byref(am), ctypes.byref(an), ctypes.byref(cm),
+                                   ctypes.byref(cn), int(bool(reset))), h)
+    return dict(agent_ms=am.value, agent_launches=an.value, consensus_ms=cm.value,
+                consensus_launches=cn.value)
+
+
+def pmace_get_plan(h):
+    p = pmace_plan()
+    _check(_lib.pmace_get_plan(h, ctypes.byref(p)), h)
+    return dict(cluster=p.cluster, threads=p.threads, smem_bytes=p.smem_bytes,
+                tile_h=p.tile_h, tile_w=p.tile_w)
+
+
+def pmace_device_bytes(h) -> int:
+    return int(_lib.pmace_device_bytes(h))
+
+
+def pmace_destroy(h):
+    _lib.pmace_destroy(h)
+
+
+def pmace_last_error(h=None) -> str:
+    return _lib.pmace_last_error(h).decode(errors="replace")
+
+
+# ----------------------------------------------------------------- wrapper
+class Reconstruction:
+    """One PMACE job resident on the current CUDA device (torch tensors in/out)."""
+
+    def __init__(self, probe, offsets, amps, image_shape, *, kappa=1.25, amp_format=PMACE_AMP_F32,
+                 scales=None, init=None, stream=None):
+        import torch
+        self.n1, self.n2 = int(image_shape[0]), int(image_shape[1])
+        self.np = int(probe.shape[0])
+        self.J = int(offsets.shape[0])
+        self.stream = stream
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self._probe = _as_pairs(probe, dev)
+        self._amps = amps if hasattr(amps, "is_cuda") and amps.is_cuda else _to_dev(amps, dev)
+        self._scales = None if scales is None else _to_dev(scales, dev).float().contiguous()
+        self._init = None if init is None else _as_pairs(init, dev)
+        self.h = pmace_create(self.n1, self.n2, self.np, self.J, kappa, self._probe, offsets,
+                              self._amps, amp_format, self._scales, self._init, True, stream)
+        self._probe = self._amps = self._scales = self._init = None
+
+    def iterate(self, n, alpha, rho=0.5):
+        pmace_iterate(self.h, n, alpha, rho, self.stream)
+
+    def image(self):
+        import torch
+        out = torch.empty((self.n1, self.n2, 2), dtype=torch.float32, device="cuda")
+        pmace_get_image(self.h, out, self.stream)
+        return torch.view_as_complex(out)
+
+    def patches(self):
+        import torch
+        out = torch.empty((self.J, self.np, self.np, 2), dtype=torch.float32, device="cuda")
+        pmace_get_patches(self.h, out, self.stream)
+        return torch.view_as_complex(out)
+
+    def residual(self):
+        return pmace_residual(self.h, self.stream)
+
+    def plan(self):
+        return pmace_get_plan(self.h)
+
+    def close(self):
+        if self.h:
+            pmace_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _to_dev(a, dev):
+    import torch
+    if isinstance(a, np.ndarray):
+        a = torch.from_numpy(np.ascontiguousarray(a))
+    return a.to(dev).contiguous()
+
+
+def _as_pairs(z, dev):
+    """Complex array -> contiguous float32 (..., 2) tensor on dev."""
+    import torch
+    if isinstance(z, np.ndarray):
+        z = torch.from_numpy(np.ascontiguousarray(z.astype(np.complex64)))
+    if z.is_complex():
+        z = torch.view_as_real(z.to(torch.complex64).contiguous())
+    return z.to(dev).float().contiguous()
