@@ -138,10 +138,14 @@ pmace_status pmace_set_profiling(pmace_handle h, int enable);
 pmace_status pmace_kernel_times(pmace_handle h, double* agent_ms, int64_t* agent_launches,
                                 double* consensus_ms, int64_t* consensus_launches, int reset);
 
-/* Kernel plan chosen for this job: cluster size (CTAs per patch) and threads
- * per CTA of the agent kernel, and the dynamic shared memory per CTA. */
+/* Kernel plan of this job: for the agent kernel the variant index, its
+ * cluster size (CTAs per window), threads per CTA, dynamic shared memory per
+ * CTA, columns per thread of the column step, whether the amplitudes are
+ * staged in shared memory, and how many clusters the device holds at once;
+ * for the consensus gather the image tile shape. */
 typedef struct {
     int32_t cluster, threads, smem_bytes, tile_h, tile_w;
+    int32_t variant, cols_per_thread, stage_y, max_clusters;
 } pmace_plan;
 pmace_status pmace_get_plan(pmace_handle h, pmace_plan* plan);
 

@@ -1,16 +1,31 @@
 // The fused agent sweep: steps S0-S5 of one PMACE iteration for every patch.
 //
 // For patch j (one cluster of C CTAs; CTA `rank` owns rows
-// [rank*Np/C, (rank+1)*Np/C) of the patch) the kernel computes, entirely in
-// shared memory and registers:
+// [rank*R, (rank+1)*R) of the Np x Np patch, R = Np/C) the kernel computes,
+// entirely in shared memory and registers:
 //   S0  v_j = q_j + 2 rho_prev P_j xbar   (closes the previous Mann step,
 //       Algorithm 1: v <- v + 2 rho (z - w) with q = v - 2 rho w, z = P_j xbar)
 //   S1  a = d . v_j
-//   S2  A = F a                 (2-D DFT, in-place DIF stages)
+//   S2  A = F a                 (2-D DFT)
 //   S3  A' = y_j A / |A|, 0 where A = 0   (Section III-A)
 //   S4  w_j = (alpha v_j + D^-1 F^* A') / (1 + alpha)   (equation F-interpolate)
 //   S5  u_j = 2 w_j - v_j (input of G), q_j <- v_j - 2 rho_cur w_j
 // and per-CTA FP64 partial sums of |z - w|^2, |w|^2, (y - |A|)^2, y^2.
+//
+// Phases (Np threads per CTA):
+//   copy-in  the CTA's amplitude rows go to shared memory with asynchronous
+//            16-byte copies while every thread streams its element pairs of
+//            q, xbar and d (16-byte loads, several pairs in flight), forms
+//            a = d . v and stores it to the tile;
+//   rows     each warp owns the rows r with r % warps == warp; the two
+//            in-place row stages touch only the warp's own rows (__syncwarp);
+//   columns  the column transform of length Np = C * R is one radix-C stage
+//            across the cluster (distributed shared memory) and an R-point
+//            DFT that each thread runs on its own column in registers,
+//            together with the magnitude replacement and the inverse DFT;
+//   copy-out the inverse row stages leave w's data term in the tile in
+//            natural order; every thread then streams its element pairs of
+//            q, xbar, 1/d and writes u and q (16-byte stores).
 #pragma once
 
 #include "fft_smem.cuh"
@@ -22,14 +37,27 @@ namespace pmace {
 
 namespace cg = cooperative_groups;
 
-template <int N, int C>
+// Geometry of one plan: N x N probe, C CTAs per patch, CPT columns per
+// thread in the column step (N / CPT threads per CTA), YST = 1 to stage the
+// amplitude rows in shared memory with asynchronous copies at kernel start
+// (0: the column step loads them itself).
+template <int N, int C, int CPT, int YST, int AMP>
 struct AgentGeom {
-    static constexpr int R = N / C;                 // rows per CTA
+    static constexpr int R = N / C;                 // rows per CTA = column DFT length
     static constexpr int RS = TileGeom<N>::RS;
-    static constexpr int kThreads = (N == 32) ? 128 : 256;
-    static constexpr int kSmem = (R * RS + N) * (int)sizeof(float2);
+    static constexpr int kThreads = N / CPT;
+    static constexpr int kWarps = kThreads / 32;
+    static constexpr int kTileBytes = R * RS * (int)sizeof(float2);
+    static constexpr int kTwBytes = N * (int)sizeof(float2);
+    static constexpr int kYBytes = YST ? R * N * (AMP ? 2 : 4) : 0;
+    static constexpr int kSmem = kTileBytes + kTwBytes + kYBytes;
     static constexpr RadixPlan kRow = radix_plan(N);
-    static constexpr RadixPlan kCol = radix_plan(R);  // local part of the column transform
+    // resident CTAs per SM the shared memory allows (228 KB per SM, 1 KB
+    // reserved per CTA plus the static reduction buffer), capped so that no
+    // thread gets fewer than 96 registers
+    static constexpr int kBySmem = (228 * 1024) / (kSmem + 2048);
+    static constexpr int kByRegs = 65536 / (kThreads * 96);
+    static constexpr int kMinBlocks = kBySmem < kByRegs ? (kBySmem > 0 ? kBySmem : 1) : kByRegs;
 };
 
 template <int AMP>
@@ -41,167 +69,256 @@ __device__ __forceinline__ float load_amp(const void* y, size_t idx, float scale
     }
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Per-CTA sums of four FP32 per-thread partials: warp sums in FP32 (32
+// terms), the warp totals added in FP64 in warp order by one thread.
 template <int T>
 __device__ __forceinline__ void block_reduce4(float (&acc)[4], double* red /* [T/32][4] */,
                                               double* out) {
-    double v[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = (double)acc[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+        for (int i = 0; i < 4; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) red[warp * 4 + i] = v[i];
+        for (int i = 0; i < 4; ++i) red[warp * 4 + i] = (double)acc[i];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s[4] = {0, 0, 0, 0};
-        for (int w = 0; w < T / 32; ++w) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) s[i] += red[w * 4 + i];
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) out[i] = s[i];
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int w = 0; w < T / 32; ++w) s += red[w * 4 + threadIdx.x];
+        out[threadIdx.x] = s;
     }
 }
 
-template <int N, int C, int AMP>
-__global__ void __launch_bounds__(AgentGeom<N, C>::kThreads)
+// Iterate over the butterflies of one row stage with radix RADIX that fall
+// on the rows this warp owns: calls f(row, m) with m the butterfly index
+// inside the row (N / RADIX per row).
+template <int N, int NROWS, int NW, int RADIX, typename F>
+__device__ __forceinline__ void for_warp_rows(F&& f) {
+    constexpr int TPR = N / RADIX;              // threads per row
+    static_assert(TPR <= 32 && 32 % TPR == 0, "a row stage must fit a warp");
+    constexpr int RPI = 32 / TPR;               // rows per warp per step
+    constexpr int ROWS_PER_WARP = NROWS / NW;
+    static_assert(NROWS % NW == 0 && ROWS_PER_WARP % RPI == 0, "rows must split evenly over warps");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < ROWS_PER_WARP / RPI; ++i) {
+        const int row = warp + NW * (i * RPI + lane / TPR);
+        f(row, lane % TPR);
+    }
+}
+
+// Element pairs (2p, 2p+1) of the CTA's rows, the unit of the copy phases:
+// pair t = threadIdx.x + i*T covers row t / (N/2), columns 2 (t % (N/2)) + {0,1}.
+template <int N, int NROWS, int T, int BATCH, typename F>
+__device__ __forceinline__ void for_pairs(F&& f) {
+    constexpr int PPT = NROWS * N / 2 / T;      // pairs per thread
+    static_assert(PPT % BATCH == 0, "pairs must split into batches");
+#pragma unroll 1
+    for (int i0 = 0; i0 < PPT; i0 += BATCH) f(i0);
+}
+
+// MINB: resident CTAs per SM the register allocation is sized for.
+template <int N, int C, int CPT, int YST, int AMP, int MINB>
+__global__ void __launch_bounds__(AgentGeom<N, C, CPT, YST, AMP>::kThreads, MINB)
 agent_kernel(const AgentArgs a) {
-    using G = AgentGeom<N, C>;
-    constexpr int R = G::R, RS = G::RS, T = G::kThreads;
+    using G = AgentGeom<N, C, CPT, YST, AMP>;
+    constexpr int R = G::R, RS = G::RS, T = G::kThreads, NW = G::kWarps;
     constexpr int r1 = G::kRow.first, r2 = G::kRow.second;
-    constexpr int c1 = G::kCol.first, c2 = G::kCol.second;
     constexpr int S1 = N / r1;
+    constexpr int HALF = N / 2;
+    constexpr int BATCH = 4;
     static_assert(r2 > 1, "row transform needs two stages");
-    static_assert(R % C == 0, "cross-CTA stage needs C | rows per CTA");
+    static_assert(R == 16 || R == 32, "column DFT length must be 16 or 32");
+    static_assert(C == 1 || R % C == 0, "cross-CTA stage needs C | rows per CTA");
 
     extern __shared__ float4 smem_raw[];
     float2* tile = reinterpret_cast<float2*>(smem_raw);
     float2* tw = tile + R * RS;
+    char* ybuf = reinterpret_cast<char*>(tw + N);
     __shared__ double red[(T / 32) * 4];
 
     int rank = 0;
     if constexpr (C > 1) rank = (int)cg::this_cluster().block_rank();
     const int j = blockIdx.x / C;
+    const size_t pbase = ((size_t)j * N + (size_t)rank * R) * N;   // first element of my rows
 
+    // ---- amplitude rows of this CTA -> shared memory, asynchronously
+    if constexpr (YST) {
+        constexpr int CH = G::kYBytes / 16;
+        const char* ysrc = static_cast<const char*>(a.y) + pbase * (AMP ? 2 : 4);
+        for (int c = threadIdx.x; c < CH; c += T) cp_async16(ybuf + 16 * c, ysrc + 16 * c);
+        cp_async_commit();
+    }
     for (int i = threadIdx.x; i < N; i += T) tw[i] = a.tw[i];
     const int2 off = a.offs[j];
-    const size_t pbase = ((size_t)j * N + (size_t)rank * R) * N;   // first element of my rows
-    float2* qp = a.q + pbase;   // read (S0) and overwritten (S5) element by element by one thread
+    float2* qp = a.q + pbase;   // read (S0) and overwritten (S5) pair by pair by one thread
     float2* __restrict__ uo = a.u + pbase;
     const float2* __restrict__ xb = a.xbar + (size_t)(off.x + rank * R) * a.n2 + off.y;
     const float2* __restrict__ pr = a.probe + (size_t)rank * R * N;
     const float2* __restrict__ di = a.dinv + (size_t)rank * R * N;
-    const size_t ybase = pbase;
-    float yscale = 1.0f;
-    if constexpr (AMP == 1) yscale = __ldg(a.yscale + j);
     const float two_rho_prev = 2.0f * a.rho_prev;
+
+    // ---- S0 + S1: a = d . (q + 2 rho_prev xbar) into the tile, natural order
+    for_pairs<N, R, T, BATCH>([&](int i0) {
+        float4 qv[BATCH], dv[BATCH];
+        float2 x0[BATCH], x1[BATCH];
+#pragma unroll
+        for (int i = 0; i < BATCH; ++i) {
+            const int t = threadIdx.x + (i0 + i) * T;
+            const int row = t / HALF, c = 2 * (t % HALF);
+            qv[i] = *reinterpret_cast<const float4*>(qp + row * N + c);
+            dv[i] = __ldg(reinterpret_cast<const float4*>(pr + row * N + c));
+            x0[i] = __ldg(xb + (size_t)row * a.n2 + c);
+            x1[i] = __ldg(xb + (size_t)row * a.n2 + c + 1);
+        }
+#pragma unroll
+        for (int i = 0; i < BATCH; ++i) {
+            const int t = threadIdx.x + (i0 + i) * T;
+            const int row = t / HALF, c = 2 * (t % HALF);
+            const float2 v0 = make_float2(fmaf(two_rho_prev, x0[i].x, qv[i].x), fmaf(two_rho_prev, x0[i].y, qv[i].y));
+            const float2 v1 = make_float2(fmaf(two_rho_prev, x1[i].x, qv[i].z), fmaf(two_rho_prev, x1[i].y, qv[i].w));
+            float2* dst = tile + row * RS + pcol(c);
+            dst[0] = cmul(make_float2(dv[i].x, dv[i].y), v0);
+            dst[1] = cmul(make_float2(dv[i].z, dv[i].w), v1);
+        }
+    });
     __syncthreads();
 
-    // ---- S0 + S1 + first row DIF stage (span N, radix r1), straight from HBM.
-    for (int t = threadIdx.x; t < R * S1; t += T) {
-        const int row = t / S1, b = t % S1;
+    // ---- row DIF: span N (radix r1), then span r2, on the warp's own rows
+    for_warp_rows<N, R, NW, r1>([&](int row, int b) {
+        float2* rp = tile + row * RS;
         float2 x[r1];
 #pragma unroll
-        for (int k = 0; k < r1; ++k) {
-            const int col = b + k * S1;
-            const float2 qv = qp[row * N + col];
-            const float2 xv = __ldg(xb + (size_t)row * a.n2 + col);
-            const float2 v = make_float2(fmaf(two_rho_prev, xv.x, qv.x), fmaf(two_rho_prev, xv.y, qv.y));
-            x[k] = cmul(__ldg(pr + row * N + col), v);
-        }
+        for (int k = 0; k < r1; ++k) x[k] = rp[pcol(b + k * S1)];
         Dft<r1, false>::run(x);
 #pragma unroll
         for (int k = 1; k < r1; ++k) x[k] = cmul(x[k], tw[b * k]);
-        float2* rp = tile + row * RS;
 #pragma unroll
         for (int k = 0; k < r1; ++k) rp[pcol(b + k * S1)] = x[k];
-    }
-    __syncthreads();
-    // ---- rest of the row DIF (span r2)
-    row_stage<N, R, r2, r2, false, T>(tile, tw);
-    __syncthreads();
+    });
+    __syncwarp();
+    for_warp_rows<N, R, NW, r2>([&](int row, int m) {
+        float2* rp = tile + row * RS;
+        float2 x[r2];
+#pragma unroll
+        for (int k = 0; k < r2; ++k) x[k] = rp[pcol(m * r2 + k)];
+        Dft<r2, false>::run(x);
+#pragma unroll
+        for (int k = 0; k < r2; ++k) rp[pcol(m * r2 + k)] = x[k];
+    });
 
-    // ---- column DIF: cross-CTA stage (span N, radix C), then local stages
-    float2* peer[C];
+    // ---- column DIF, cross-CTA stage (span N, radix C)
     if constexpr (C > 1) {
         cg::cluster_group cl = cg::this_cluster();
-#pragma unroll
-        for (int k = 0; k < C; ++k) peer[k] = cl.map_shared_rank(tile, k);
         cl.sync();
-        cross_stage<N, R, C, false, T>(peer, tw, rank);
+        cross_stage<N, R, C, false, T>(tile, tw, rank);
+        cp_async_wait_all();
         cl.sync();
-    }
-    if constexpr (c2 > 1) {
-        col_stage<N, R, R, c1, false, T>(tile, tw);
+    } else {
+        cp_async_wait_all();
         __syncthreads();
     }
 
-    // ---- last column DIF stage + S3 magnitude replacement + first column DIT stage
+    // ---- R-point column DFT in registers + S3 + inverse R-point DFT.
+    // Thread `col` (CPT columns per thread) holds local rows 0..R-1 of its
+    // column; after the forward
+    // DFT register k2 holds frequency row rank + C*k2, which is where the
+    // amplitudes were stored (kernel order: row rank*R + k2).
     float acc_d = 0.f, acc_y = 0.f;
-    {
-        constexpr int rl = (c2 > 1) ? c2 : c1;
-        constexpr int NB = (R / rl) * N;
-        const float inv_n = 1.0f / (float)N;
-        for (int t = threadIdx.x; t < NB; t += T) {
-            const int col = t % N, rbase = (t / N) * rl;
-            float2* cp = tile + pcol(col);
-            float2 x[rl];
+    float yscale = 1.0f;
+    if constexpr (AMP == 1) yscale = __ldg(a.yscale + j);
+#pragma unroll 1
+    for (int ci = 0; ci < CPT; ++ci) {
+        const int col = threadIdx.x + ci * T;
+        float yv[R];
 #pragma unroll
-            for (int k = 0; k < rl; ++k) x[k] = cp[(rbase + k) * RS];
-            Dft<rl, false>::run(x);
-#pragma unroll
-            for (int k = 0; k < rl; ++k) {
-                const float yv = load_amp<AMP>(a.y, ybase + (size_t)(rbase + k) * N + col, yscale);
-                // phase A/|A| (0 only where A = 0); coefficients whose squared
-                // magnitude would underflow are rescaled by 2^100 first
-                float2 xa = x[k];
-                float m2 = fmaf(xa.x, xa.x, xa.y * xa.y);
-                float unscale = inv_n;
-                if (m2 < 0x1p-100f) {
-                    xa = xa * 0x1p100f;
-                    m2 = fmaf(xa.x, xa.x, xa.y * xa.y);
-                    unscale = inv_n * 0x1p-100f;
-                }
-                float2 o = make_float2(0.f, 0.f);
-                float mag = 0.f;
-                if (m2 > 0.f) {
-                    const float rs = rsqrtf(m2);
-                    mag = m2 * rs * unscale;
-                    o = xa * (yv * rs);
-                }
-                const float e = yv - mag;
-                acc_d = fmaf(e, e, acc_d);
-                acc_y = fmaf(yv, yv, acc_y);
-                x[k] = o;
+        for (int k = 0; k < R; ++k) {
+            if constexpr (YST) {
+                if constexpr (AMP == 0) yv[k] = reinterpret_cast<const float*>(ybuf)[k * N + col];
+                else yv[k] = __half2float(reinterpret_cast<const __half*>(ybuf)[k * N + col]) * yscale;
+            } else {
+                yv[k] = load_amp<AMP>(a.y, pbase + (size_t)k * N + col, yscale);
             }
-            Dft<rl, true>::run(x);
-#pragma unroll
-            for (int k = 0; k < rl; ++k) cp[(rbase + k) * RS] = x[k];
         }
+        float2* cp = tile + pcol(col);
+        float2 x[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) x[k] = cp[k * RS];
+        Dft<R, false>::run(x);
+        const float inv_n = 1.0f / (float)N;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            // phase A/|A| (0 only where A = 0); coefficients whose squared
+            // magnitude would underflow are rescaled by 2^100 first
+            float2 xa = x[k];
+            float m2 = fmaf(xa.x, xa.x, xa.y * xa.y);
+            float unscale = inv_n;
+            if (m2 < 0x1p-100f) {
+                xa = xa * 0x1p100f;
+                m2 = fmaf(xa.x, xa.x, xa.y * xa.y);
+                unscale = inv_n * 0x1p-100f;
+            }
+            float2 o = make_float2(0.f, 0.f);
+            float mag = 0.f;
+            if (m2 > 0.f) {
+                const float rs = rsqrtf(m2);
+                mag = m2 * rs * unscale;
+                o = xa * (yv[k] * rs);
+            }
+            const float e = yv[k] - mag;
+            acc_d = fmaf(e, e, acc_d);
+            acc_y = fmaf(yv[k], yv[k], acc_y);
+            x[k] = o;
+        }
+        Dft<R, true>::run(x);
+#pragma unroll
+        for (int k = 0; k < R; ++k) cp[k * RS] = x[k];
     }
-    __syncthreads();
 
-    // ---- column DIT: remaining local stage, then the cross-CTA stage
-    if constexpr (c2 > 1) {
-        col_stage<N, R, R, c1, true, T>(tile, tw);
-        __syncthreads();
-    }
+    // ---- column DIT, cross-CTA stage
     if constexpr (C > 1) {
         cg::cluster_group cl = cg::this_cluster();
         cl.sync();
-        cross_stage<N, R, C, true, T>(peer, tw, rank);
+        cross_stage<N, R, C, true, T>(tile, tw, rank);
         cl.sync();   // also keeps every tile alive until the peers are done with it
+    } else {
+        __syncthreads();
     }
-    // ---- row DIT (span r2), then the last row stage fused with S4 + S5
-    row_stage<N, R, r2, r2, true, T>(tile, tw);
+
+    // ---- row DIT: span r2, then span N; result back in the tile, natural order
+    for_warp_rows<N, R, NW, r2>([&](int row, int m) {
+        float2* rp = tile + row * RS;
+        float2 x[r2];
+#pragma unroll
+        for (int k = 0; k < r2; ++k) x[k] = rp[pcol(m * r2 + k)];
+        Dft<r2, true>::run(x);
+#pragma unroll
+        for (int k = 0; k < r2; ++k) rp[pcol(m * r2 + k)] = x[k];
+    });
+    __syncwarp();
+    for_warp_rows<N, R, NW, r1>([&](int row, int b) {
+        float2* rp = tile + row * RS;
+        float2 x[r1];
+#pragma unroll
+        for (int k = 0; k < r1; ++k) x[k] = rp[pcol(b + k * S1)];
+#pragma unroll
+        for (int k = 1; k < r1; ++k) x[k] = cmulc(x[k], tw[b * k]);
+        Dft<r1, true>::run(x);
+#pragma unroll
+        for (int k = 0; k < r1; ++k) rp[pcol(b + k * S1)] = x[k];
+    });
     __syncthreads();
 
+    // ---- S4 + S5, pair by pair
     float acc_z = 0.f, acc_w = 0.f;
     {
         const float scale = 1.0f / (float)N;          // orthonormal F^*
@@ -209,49 +326,55 @@ agent_kernel(const AgentArgs a) {
         const float alpha = a.alpha;
         const float two_rho = 2.0f * a.rho_cur;
         const bool first = a.first != 0;
-        for (int t = threadIdx.x; t < R * S1; t += T) {
-            const int row = t / S1, b = t % S1;
-            const float2* rp = tile + row * RS;
-            float2 x[r1];
-#pragma unroll
-            for (int k = 0; k < r1; ++k) x[k] = rp[pcol(b + k * S1)];
-#pragma unroll
-            for (int k = 1; k < r1; ++k) x[k] = cmulc(x[k], tw[b * k]);
-            Dft<r1, true>::run(x);
-#pragma unroll
-            for (int k = 0; k < r1; ++k) {
-                const int col = b + k * S1;
-                const int e = row * N + col;
-                const float2 qv = qp[e];
-                const float2 xv = __ldg(xb + (size_t)row * a.n2 + col);
-                const float2 v = make_float2(fmaf(two_rho_prev, xv.x, qv.x), fmaf(two_rho_prev, xv.y, qv.y));
-                const float2 dv = __ldg(di + e);
-                float2 w;
-                if (dv.x == 0.f && dv.y == 0.f) {
-                    w = v;                                    // d treated as absent here
-                } else {
-                    const float2 g = cmul(dv, x[k] * scale);  // D^-1 F^* A'
-                    w = make_float2(fmaf(alpha, v.x, g.x) * inv1pa, fmaf(alpha, v.y, g.y) * inv1pa);
-                }
-                const float2 uu = make_float2(2.f * w.x - v.x, 2.f * w.y - v.y);
-                const float2 qn = make_float2(fmaf(-two_rho, w.x, v.x), fmaf(-two_rho, w.y, v.y));
-                const float2 z = first ? v : xv;
-                const float dzx = z.x - w.x, dzy = z.y - w.y;
-                acc_z = fmaf(dzx, dzx, fmaf(dzy, dzy, acc_z));
-                acc_w = fmaf(w.x, w.x, fmaf(w.y, w.y, acc_w));
-                uo[e] = uu;
-                qp[e] = qn;
+        auto agent_update = [&](float2 g, float2 q, float2 xv, float2 dv, float2& u, float2& qn) {
+            const float2 v = make_float2(fmaf(two_rho_prev, xv.x, q.x), fmaf(two_rho_prev, xv.y, q.y));
+            float2 w;
+            if (dv.x == 0.f && dv.y == 0.f) {
+                w = v;                                    // d treated as absent here
+            } else {
+                const float2 h = cmul(dv, g * scale);     // D^-1 F^* A'
+                w = make_float2(fmaf(alpha, v.x, h.x) * inv1pa, fmaf(alpha, v.y, h.y) * inv1pa);
             }
-        }
+            u = make_float2(2.f * w.x - v.x, 2.f * w.y - v.y);
+            qn = make_float2(fmaf(-two_rho, w.x, v.x), fmaf(-two_rho, w.y, v.y));
+            const float2 z = first ? v : xv;
+            const float dzx = z.x - w.x, dzy = z.y - w.y;
+            acc_z = fmaf(dzx, dzx, fmaf(dzy, dzy, acc_z));
+            acc_w = fmaf(w.x, w.x, fmaf(w.y, w.y, acc_w));
+        };
+        for_pairs<N, R, T, BATCH>([&](int i0) {
+            float4 qv[BATCH], dv[BATCH];
+            float2 x0[BATCH], x1[BATCH];
+#pragma unroll
+            for (int i = 0; i < BATCH; ++i) {
+                const int t = threadIdx.x + (i0 + i) * T;
+                const int row = t / HALF, c = 2 * (t % HALF);
+                qv[i] = *reinterpret_cast<const float4*>(qp + row * N + c);
+                dv[i] = __ldg(reinterpret_cast<const float4*>(di + row * N + c));
+                x0[i] = __ldg(xb + (size_t)row * a.n2 + c);
+                x1[i] = __ldg(xb + (size_t)row * a.n2 + c + 1);
+            }
+#pragma unroll
+            for (int i = 0; i < BATCH; ++i) {
+                const int t = threadIdx.x + (i0 + i) * T;
+                const int row = t / HALF, c = 2 * (t % HALF);
+                const float2* src = tile + row * RS + pcol(c);
+                float2 u0, u1, q0, q1;
+                agent_update(src[0], make_float2(qv[i].x, qv[i].y), x0[i], make_float2(dv[i].x, dv[i].y), u0, q0);
+                agent_update(src[1], make_float2(qv[i].z, qv[i].w), x1[i], make_float2(dv[i].z, dv[i].w), u1, q1);
+                *reinterpret_cast<float4*>(uo + row * N + c) = make_float4(u0.x, u0.y, u1.x, u1.y);
+                *reinterpret_cast<float4*>(qp + row * N + c) = make_float4(q0.x, q0.y, q1.x, q1.y);
+            }
+        });
     }
     float acc[4] = {acc_z, acc_w, acc_d, acc_y};
     block_reduce4<T>(acc, red, a.partials + ((size_t)j * C + rank) * 4);
 }
 
-template <int N, int C>
-cudaError_t launch_agent_impl(const AgentArgs& a, int amp_f16, cudaStream_t s) {
-    using G = AgentGeom<N, C>;
-    void (*fn)(const AgentArgs) = amp_f16 ? agent_kernel<N, C, 1> : agent_kernel<N, C, 0>;
+template <int N, int C, int CPT, int YST, int AMP, int MINB>
+cudaError_t launch_agent_impl(const AgentArgs& a, cudaStream_t s) {
+    using G = AgentGeom<N, C, CPT, YST, AMP>;
+    void (*fn)(const AgentArgs) = agent_kernel<N, C, CPT, YST, AMP, MINB>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem);
     if (e != cudaSuccess) return e;
     if constexpr (C > 1) {
@@ -273,32 +396,29 @@ cudaError_t launch_agent_impl(const AgentArgs& a, int amp_f16, cudaStream_t s) {
     return cudaLaunchKernelEx(&cfg, fn, a);
 }
 
-template <int N, int C>
-bool plan_launchable_impl();
-
-template <int N, int C>
-cudaError_t agent_entry_impl(const AgentArgs* a, int amp_f16, cudaStream_t s, AgentPlanInfo* info) {
-    using G = AgentGeom<N, C>;
-    if (a == nullptr) {
-        if (info) {
-            info->threads = G::kThreads;
-            info->smem_bytes = G::kSmem;
-            info->launchable = plan_launchable_impl<N, C>() ? 1 : 0;
-        }
-        return cudaSuccess;
+// How many clusters of this plan the device holds at once (0: not launchable).
+template <int N, int C, int CPT, int YST, int AMP, int MINB>
+int plan_max_clusters_impl() {
+    using G = AgentGeom<N, C, CPT, YST, AMP>;
+    void (*fn)(const AgentArgs) = agent_kernel<N, C, CPT, YST, AMP, MINB>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
     }
-    return launch_agent_impl<N, C>(*a, amp_f16, s);
-}
-
-template <int N, int C>
-bool plan_launchable_impl() {
-    using G = AgentGeom<N, C>;
-    void (*fn)(const AgentArgs) = agent_kernel<N, C, 0>;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem) != cudaSuccess)
-        return false;
-    if (C == 1) return true;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-        return false;
+    if (C == 1) {
+        int per_sm = 0, dev = 0, nsm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, G::kThreads, G::kSmem) != cudaSuccess ||
+            cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return per_sm * nsm;
+    }
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(C * 64), 1, 1);
     cfg.blockDim = dim3(G::kThreads, 1, 1);
@@ -313,9 +433,34 @@ bool plan_launchable_impl() {
     int nclusters = 0;
     if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return nclusters > 0;
+    return nclusters;
+}
+
+// One plan: query (a == nullptr) or launch, for either amplitude format.
+template <int N, int C, int CPT, int YST>
+cudaError_t agent_variant(const AgentArgs* a, int amp_f16, cudaStream_t s, AgentPlanInfo* info) {
+    if (amp_f16) {
+        using G = AgentGeom<N, C, CPT, YST, 1>;
+        if (a == nullptr) {
+            info->threads = G::kThreads;
+            info->smem_bytes = G::kSmem;
+            info->max_clusters = plan_max_clusters_impl<N, C, CPT, YST, 1, G::kMinBlocks>();
+            info->launchable = info->max_clusters > 0;
+            return cudaSuccess;
+        }
+        return launch_agent_impl<N, C, CPT, YST, 1, G::kMinBlocks>(*a, s);
+    }
+    using G = AgentGeom<N, C, CPT, YST, 0>;
+    if (a == nullptr) {
+        info->threads = G::kThreads;
+        info->smem_bytes = G::kSmem;
+        info->max_clusters = plan_max_clusters_impl<N, C, CPT, YST, 0, G::kMinBlocks>();
+        info->launchable = info->max_clusters > 0;
+        return cudaSuccess;
+    }
+    return launch_agent_impl<N, C, CPT, YST, 0, G::kMinBlocks>(*a, s);
 }
 
 }  // namespace pmace

@@ -26,38 +26,44 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
 }
 
-// cos(2 pi m / 16), sin(2 pi m / 16) for m = 0..15, as exact decimal values
-// of the mathematical constants (rounded to float at compile time).
-__host__ __device__ constexpr double k_cos16(int m) {
-    constexpr double c1 = 0.92387953251128675613, c2 = 0.70710678118654752440,
-                     c3 = 0.38268343236508977173;
-    constexpr double t[16] = {1.0, c1, c2, c3, 0.0, -c3, -c2, -c1,
-                              -1.0, -c1, -c2, -c3, 0.0, c3, c2, c1};
-    return t[m & 15];
+// cos(2 pi m / 32) for m = 0..31, built from cos(pi k / 16), k = 0..8, given
+// as decimal values of the mathematical constants (rounded at compile time).
+__host__ __device__ constexpr double k_cos32(int m) {
+    constexpr double c[9] = {1.0,
+                             0.98078528040323044913,
+                             0.92387953251128675613,
+                             0.83146961230254523708,
+                             0.70710678118654752440,
+                             0.55557023301960222474,
+                             0.38268343236508977173,
+                             0.19509032201612826785,
+                             0.0};
+    const int k = m & 31;                        // angle 2 pi k / 32 = pi k / 16
+    return k <= 8 ? c[k] : k <= 16 ? -c[16 - k] : k <= 24 ? -c[k - 16] : c[32 - k];
 }
-__host__ __device__ constexpr double k_sin16(int m) { return k_cos16((m + 12) & 15); }
+__host__ __device__ constexpr double k_sin32(int m) { return k_cos32((m + 24) & 31); }
 
-// a * W_16^M with W_16 = exp(-2 pi i / 16) (forward) or exp(+2 pi i / 16)
-// (INV); trivial factors are applied without multiplications.
-template <int M, bool INV>
-__device__ __forceinline__ float2 twiddle16(float2 a) {
-    constexpr int m = M & 15;
+// a * W_D^M with W_D = exp(-2 pi i / D) (forward) or exp(+2 pi i / D) (INV),
+// D in {2, 4, 8, 16, 32}; trivial factors are applied without multiplications.
+template <int M, int D, bool INV>
+__device__ __forceinline__ float2 twiddle(float2 a) {
+    constexpr int m = (M * (32 / D)) & 31;      // in units of 2 pi / 32
     if constexpr (m == 0) {
         return a;
-    } else if constexpr (m == 8) {
+    } else if constexpr (m == 16) {
         return make_float2(-a.x, -a.y);
-    } else if constexpr ((m == 4 && !INV) || (m == 12 && INV)) {
+    } else if constexpr ((m == 8 && !INV) || (m == 24 && INV)) {
         return make_float2(a.y, -a.x);   // * (-i)
-    } else if constexpr ((m == 12 && !INV) || (m == 4 && INV)) {
+    } else if constexpr ((m == 24 && !INV) || (m == 8 && INV)) {
         return make_float2(-a.y, a.x);   // * (+i)
     } else {
-        constexpr float c = (float)k_cos16(m);
-        constexpr float s = INV ? (float)k_sin16(m) : -(float)k_sin16(m);
+        constexpr float c = (float)k_cos32(m);
+        constexpr float s = INV ? (float)k_sin32(m) : -(float)k_sin32(m);
         return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
     }
 }
 
-// In-register DFT of length R (2, 4, 8, 16), natural order in and out:
+// In-register DFT of length R (2, 4, 8, 16, 32), natural order in and out:
 // X[k] = sum_j x[j] exp(-+2 pi i j k / R).
 template <int R, bool INV>
 struct Dft;
@@ -75,7 +81,7 @@ template <bool INV>
 struct Dft<4, INV> {
     __device__ __forceinline__ static void run(float2 (&x)[4]) {
         float2 a = x[0] + x[2], b = x[0] - x[2], c = x[1] + x[3];
-        float2 d = twiddle16<4, INV>(x[1] - x[3]);
+        float2 d = twiddle<1, 4, INV>(x[1] - x[3]);
         x[0] = a + c;
         x[2] = a - c;
         x[1] = b + d;
@@ -99,7 +105,7 @@ struct FourStep {
     template <int J2, int K1>
     __device__ __forceinline__ static void apply_tw(const float2 (&s)[R1], float2 (&t)[R]) {
         if constexpr (K1 < R1) {
-            t[J2 * R1 + K1] = twiddle16<(J2 * K1 * (16 / R)), INV>(s[K1]);
+            t[J2 * R1 + K1] = twiddle<J2 * K1, R, INV>(s[K1]);
             apply_tw<J2, K1 + 1>(s, t);
         }
     }
@@ -135,6 +141,11 @@ struct Dft<16, INV> {
     __device__ __forceinline__ static void run(float2 (&x)[16]) { FourStep<4, 4, INV>::run(x); }
 };
 
+template <bool INV>
+struct Dft<32, INV> {
+    __device__ __forceinline__ static void run(float2 (&x)[32]) { FourStep<8, 4, INV>::run(x); }
+};
+
 // Padded shared-memory column index: one float2 of padding after every 16,
 // which makes the stride-16 accesses of the short-span stages conflict free.
 __device__ __forceinline__ int pcol(int c) { return c + (c >> 4); }
@@ -143,79 +154,23 @@ struct TileGeom {
     static constexpr int RS = N + N / 16;  // padded row stride in float2
 };
 
-// Forward twiddle W_N^m = exp(-2 pi i m / N) from a table tw[0..N).
-template <bool INV>
-__device__ __forceinline__ float2 apply_table_tw(float2 a, float2 w) {
-    return INV ? cmulc(a, w) : cmul(a, w);
+// Distributed shared memory access through 32-bit shared::cluster addresses.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-
-// One in-place radix-R stage along the row axis (inside each row of the
-// tile), span L, for NROWS rows of length N.  DIF: butterfly then twiddle
-// W_L^{b k}; DIT (INV): conjugate twiddle then inverse butterfly.
-template <int N, int NROWS, int L, int R, bool INV, int T>
-__device__ __forceinline__ void row_stage(float2* __restrict__ tile, const float2* __restrict__ tw) {
-    constexpr int RS = TileGeom<N>::RS;
-    constexpr int S = L / R;
-    constexpr int BPR = N / R;
-    constexpr int NB = NROWS * BPR;
-    for (int t = threadIdx.x; t < NB; t += T) {
-        const int row = t / BPR, m = t % BPR;
-        const int b = m % S;
-        const int base = (m / S) * L + b;
-        float2* rp = tile + row * RS;
-        float2 x[R];
-#pragma unroll
-        for (int k = 0; k < R; ++k) x[k] = rp[pcol(base + k * S)];
-        if constexpr (INV) {
-            if constexpr (S > 1) {
-#pragma unroll
-                for (int k = 1; k < R; ++k) x[k] = cmulc(x[k], tw[b * k * (N / L)]);
-            }
-            Dft<R, true>::run(x);
-        } else {
-            Dft<R, false>::run(x);
-            if constexpr (S > 1) {
-#pragma unroll
-                for (int k = 1; k < R; ++k) x[k] = cmul(x[k], tw[b * k * (N / L)]);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < R; ++k) rp[pcol(base + k * S)] = x[k];
-    }
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
 }
-
-// One in-place radix-R stage along the column axis inside the CTA's own
-// NROWS rows, span L <= NROWS, of a length-N column transform (twiddles from
-// the same length-N table).
-template <int N, int NROWS, int L, int R, bool INV, int T>
-__device__ __forceinline__ void col_stage(float2* __restrict__ tile, const float2* __restrict__ tw) {
-    constexpr int RS = TileGeom<N>::RS;
-    constexpr int S = L / R;
-    constexpr int NB = (NROWS / R) * N;
-    for (int t = threadIdx.x; t < NB; t += T) {
-        const int col = t % N, m = t / N;
-        const int b = m % S;
-        const int rbase = (m / S) * L + b;
-        float2* cp = tile + pcol(col);
-        float2 x[R];
-#pragma unroll
-        for (int k = 0; k < R; ++k) x[k] = cp[(rbase + k * S) * RS];
-        if constexpr (INV) {
-            if constexpr (S > 1) {
-#pragma unroll
-                for (int k = 1; k < R; ++k) x[k] = cmulc(x[k], tw[b * k * (N / L)]);
-            }
-            Dft<R, true>::run(x);
-        } else {
-            Dft<R, false>::run(x);
-            if constexpr (S > 1) {
-#pragma unroll
-                for (int k = 1; k < R; ++k) x[k] = cmul(x[k], tw[b * k * (N / L)]);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < R; ++k) cp[(rbase + k * S) * RS] = x[k];
-    }
+__device__ __forceinline__ float2 ld_cluster(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
 
 // The column-axis stage of span N and radix C across the C CTAs of a
@@ -223,20 +178,21 @@ __device__ __forceinline__ void col_stage(float2* __restrict__ tile, const float
 // at local row b combines row b of every CTA.  Each CTA takes NROWS/C of the
 // butterflies, reading and writing the peers' tiles through distributed
 // shared memory; a butterfly's elements are read and written by one thread
-// only, so the stage is in place without staging.
+// only, so the stage is in place without staging.  `tile` is this CTA's
+// tile; the peers' copies are addressed through mapa.
 template <int N, int NROWS, int C, bool INV, int T>
-__device__ __forceinline__ void cross_stage(float2* const (&peer)[C], const float2* __restrict__ tw,
-                                            int rank) {
+__device__ __forceinline__ void cross_stage(const float2* tile, const float2* __restrict__ tw, int rank) {
+    const uint32_t mine = smem_addr(tile);
     constexpr int RS = TileGeom<N>::RS;
     constexpr int BR = NROWS / C;     // butterfly rows per CTA
     constexpr int NB = BR * N;
     for (int t = threadIdx.x; t < NB; t += T) {
         const int col = t % N;
         const int b = rank * BR + t / N;
-        const int off = b * RS + pcol(col);
+        const uint32_t off = (uint32_t)(b * RS + pcol(col)) * (uint32_t)sizeof(float2);
         float2 x[C];
 #pragma unroll
-        for (int k = 0; k < C; ++k) x[k] = peer[k][off];
+        for (int k = 0; k < C; ++k) x[k] = ld_cluster(cluster_addr(mine + off, (uint32_t)k));
         if constexpr (INV) {
 #pragma unroll
             for (int k = 1; k < C; ++k) x[k] = cmulc(x[k], tw[b * k]);
@@ -247,7 +203,7 @@ __device__ __forceinline__ void cross_stage(float2* const (&peer)[C], const floa
             for (int k = 1; k < C; ++k) x[k] = cmul(x[k], tw[b * k]);
         }
 #pragma unroll
-        for (int k = 0; k < C; ++k) peer[k][off] = x[k];
+        for (int k = 0; k < C; ++k) st_cluster(cluster_addr(mine + off, (uint32_t)k), x[k]);
     }
 }
 

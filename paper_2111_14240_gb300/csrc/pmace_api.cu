@@ -9,7 +9,7 @@
 // plus the probe tables (d, 1/d, |d|^kappa, twiddles) and the scan-overlap
 // lists.  One iteration of Algorithm 1 is two launches: the fused agent
 // sweep (agent.cuh) and the pixel-owner consensus gather (support.cu).
-#include "../../include/pmace.h"
+#include "pmace.h"
 #include "pmace_internal.h"
 
 #include <cuda_fp16.h>
@@ -45,6 +45,7 @@ struct pmace_job {
     pmace_dims dims{};
     int amp_f16 = 0;
     int cluster = 1;
+    int variant = 0;
     AgentPlanInfo plan{};
     int tiles_x = 0, tiles_y = 0, ntiles = 0;
 
@@ -101,25 +102,40 @@ cudaError_t dalloc(pmace_job* h, T** p, size_t count) {
 
 bool np_supported(int np) { return np == 32 || np == 64 || np == 128 || np == 256; }
 
-cudaError_t agent_entry(int np, const AgentArgs* a, int cluster, int amp, cudaStream_t s,
+cudaError_t agent_entry(int np, const AgentArgs* a, int variant, int amp, cudaStream_t s,
                         AgentPlanInfo* info) {
     switch (np) {
-        case 32: return agent_entry_32(a, cluster, amp, s, info);
-        case 64: return agent_entry_64(a, cluster, amp, s, info);
-        case 128: return agent_entry_128(a, cluster, amp, s, info);
-        case 256: return agent_entry_256(a, cluster, amp, s, info);
+        case 32: return agent_entry_32(a, variant, amp, s, info);
+        case 64: return agent_entry_64(a, variant, amp, s, info);
+        case 128: return agent_entry_128(a, variant, amp, s, info);
+        case 256: return agent_entry_256(a, variant, amp, s, info);
         default: return cudaErrorInvalidValue;
     }
 }
 
-// Default CTAs per patch for each probe size (the smallest cluster whose
-// tile leaves room for more than one resident CTA per SM).
-int default_cluster(int np) {
+// Agent variant to start from: PMACE_AGENT_PLAN (an index into
+// agent_variant_of) when set and valid, else PMACE_AGENT_CLUSTER selects the
+// first variant with that cluster size, else variant 0.
+int default_variant(int np) {
+    if (const char* env = std::getenv("PMACE_AGENT_PLAN")) {
+        const int v = std::atoi(env);
+        if (v >= 0 && v < kAgentVariants) return v;
+    }
     if (const char* env = std::getenv("PMACE_AGENT_CLUSTER")) {
         const int c = std::atoi(env);
-        if (c > 0) return c;
+        for (int v = 0; v < kAgentVariants; ++v)
+            if (agent_variant_of(np, v).cluster == c) return v;
     }
-    return np == 256 ? 8 : np == 128 ? 2 : 1;
+    return 0;
+}
+
+// Row order of the amplitudes for a cluster size: kernel row g holds
+// frequency row (g / rows) + cluster * (g % rows), rows = np / cluster.
+std::vector<int> column_order(int np, int cluster) {
+    std::vector<int> perm(np);
+    const int rows = np / cluster;
+    for (int g = 0; g < np; ++g) perm[g] = g / rows + cluster * (g % rows);
+    return perm;
 }
 
 // Frequency index held at each position after in-place DIF stages with the
@@ -200,13 +216,12 @@ pmace_status build_tables(pmace_job* h, const std::vector<float>& probe_h,
         for (int ty = y0; ty <= y1; ++ty)
             for (int tx = x0; tx <= x1; ++tx) list[fill[ty * h->tiles_x + tx]++] = j;
     }
-    // row and column spectra orders of the agent kernel
-    std::vector<int> rowperm, colperm;
+    // row and column spectrum orders of the agent kernel: the two in-place
+    // row stages leave each row digit-reversed; along columns, local row k2
+    // of CTA `rank` holds frequency rank + cluster * k2 after the cross-CTA
+    // stage and the in-register column DFT
+    std::vector<int> rowperm, colperm = column_order(np, h->cluster);
     dif_order(radices_of(np), 0, np, rowperm);
-    std::vector<int> crad;
-    if (h->cluster > 1) crad.push_back(h->cluster);
-    for (int r : radices_of(np / h->cluster)) crad.push_back(r);
-    dif_order(crad, 0, np, colperm);
 
     PM_CUDA(h, dalloc(h, &h->probe, P));
     PM_CUDA(h, dalloc(h, &h->dinv, P));
@@ -351,18 +366,24 @@ pmace_status pmace_create(const pmace_dims* dims, const float* probe, const int3
         return st;
     };
 
-    // plan: requested cluster if it exists and fits, else the next smaller one
-    int c = std::min(default_cluster(np), kMaxCluster);
-    for (; c >= 1; c >>= 1) {
-        AgentPlanInfo info{};
-        if (agent_entry(np, nullptr, c, 0, s, &info) == cudaSuccess && info.launchable) {
-            h->plan = info;
-            break;
+    // plan: the requested variant if the device can run it, else the first that it can
+    {
+        const int v0 = default_variant(np);
+        int chosen = -1;
+        for (int i = 0; i < kAgentVariants && chosen < 0; ++i) {
+            const int v = (v0 + i) % kAgentVariants;
+            AgentPlanInfo info{};
+            if (agent_entry(np, nullptr, v, h->amp_f16, s, &info) == cudaSuccess && info.launchable) {
+                h->plan = info;
+                chosen = v;
+            }
+            cudaGetLastError();
         }
-        cudaGetLastError();
+        if (chosen < 0)
+            return bail(fail(h, PMACE_ERR_UNSUPPORTED_SIZE, "no launchable agent plan for np=%d", np));
+        h->variant = chosen;
+        h->cluster = agent_variant_of(np, chosen).cluster;
     }
-    if (c < 1) return bail(fail(h, PMACE_ERR_UNSUPPORTED_SIZE, "no launchable agent plan for np=%d", np));
-    h->cluster = c;
 
     // host copies of the small inputs
     std::vector<float> probe_h(2 * P);
@@ -489,7 +510,7 @@ pmace_status pmace_iterate(pmace_handle h, int32_t n, const pmace_step* step, vo
         a.rho_prev = h->rho_pending;
         a.first = h->iterations == 0 ? 1 : 0;
         if (h->profiling) PM_CUDA(h, record_pair(h->ev_agent, h->n_agent, true, s));
-        PM_CUDA(h, agent_entry(h->dims.np, &a, h->cluster, h->amp_f16, s, nullptr));
+        PM_CUDA(h, agent_entry(h->dims.np, &a, h->variant, h->amp_f16, s, nullptr));
         if (h->profiling) {
             PM_CUDA(h, record_pair(h->ev_agent, h->n_agent, false, s));
             PM_CUDA(h, record_pair(h->ev_cons, h->n_cons, true, s));
@@ -622,11 +643,16 @@ pmace_status pmace_kernel_times(pmace_handle h, double* agent_ms, int64_t* agent
 pmace_status pmace_get_plan(pmace_handle h, pmace_plan* plan) {
     if (!h) return fail(nullptr, PMACE_ERR_INVALID_ARG, "NULL handle");
     if (!plan) return fail(h, PMACE_ERR_INVALID_ARG, "plan is NULL");
+    const AgentVariant v = agent_variant_of(h->dims.np, h->variant);
     plan->cluster = h->cluster;
     plan->threads = h->plan.threads;
     plan->smem_bytes = h->plan.smem_bytes;
     plan->tile_h = kGatherTileH;
     plan->tile_w = kGatherTileW;
+    plan->variant = h->variant;
+    plan->cols_per_thread = v.cols_per_thread;
+    plan->stage_y = v.stage_y;
+    plan->max_clusters = h->plan.max_clusters;
     return PMACE_OK;
 }
 

@@ -59,20 +59,37 @@ constexpr int kGatherTileH = 32;
 constexpr int kGatherTileW = 32;
 constexpr int kGatherThreads = 256;
 
+// Agent kernel variants compiled for each probe size: CTAs per patch,
+// columns per thread in the column step, amplitude staging in shared memory.
+// Index 0 is the default; pmace_autotune and PMACE_AGENT_PLAN pick others.
+struct AgentVariant {
+    int cluster, cols_per_thread, stage_y;
+};
+constexpr int kAgentVariants = 4;
+__host__ __device__ constexpr AgentVariant agent_variant_of(int np, int v) {
+    constexpr AgentVariant t32[kAgentVariants] = {{2, 1, 1}, {1, 1, 1}, {2, 1, 0}, {1, 1, 0}};
+    constexpr AgentVariant t64[kAgentVariants] = {{4, 1, 1}, {4, 2, 0}, {2, 1, 1}, {4, 1, 0}};
+    constexpr AgentVariant t128[kAgentVariants] = {{8, 1, 1}, {8, 2, 0}, {4, 1, 1}, {8, 1, 0}};
+    constexpr AgentVariant t256[kAgentVariants] = {{16, 2, 0}, {16, 1, 1}, {8, 1, 1}, {8, 2, 0}};
+    return np == 32 ? t32[v] : np == 64 ? t64[v] : np == 128 ? t128[v] : t256[v];
+}
+
 // Geometry of one agent plan (probe size, CTAs per patch).
 struct AgentPlanInfo {
     int threads;      // threads per CTA
     int smem_bytes;   // dynamic shared memory per CTA
     int launchable;   // the device can co-schedule at least one cluster
+    int max_clusters; // clusters the device can hold at once
 };
 
 // Agent entry points, one per probe size (each in its own translation unit).
-// With a == nullptr they only fill `info` (cudaErrorInvalidValue if the
-// (np, cluster) pair has no instantiation); otherwise they launch the sweep.
-cudaError_t agent_entry_32(const AgentArgs* a, int cluster, int amp_f16, cudaStream_t s, AgentPlanInfo* info);
-cudaError_t agent_entry_64(const AgentArgs* a, int cluster, int amp_f16, cudaStream_t s, AgentPlanInfo* info);
-cudaError_t agent_entry_128(const AgentArgs* a, int cluster, int amp_f16, cudaStream_t s, AgentPlanInfo* info);
-cudaError_t agent_entry_256(const AgentArgs* a, int cluster, int amp_f16, cudaStream_t s, AgentPlanInfo* info);
+// With a == nullptr they only fill `info` for variant `v` of
+// agent_variant_of (cudaErrorInvalidValue for an unknown variant);
+// otherwise they launch the sweep.
+cudaError_t agent_entry_32(const AgentArgs* a, int v, int amp_f16, cudaStream_t s, AgentPlanInfo* info);
+cudaError_t agent_entry_64(const AgentArgs* a, int v, int amp_f16, cudaStream_t s, AgentPlanInfo* info);
+cudaError_t agent_entry_128(const AgentArgs* a, int v, int amp_f16, cudaStream_t s, AgentPlanInfo* info);
+cudaError_t agent_entry_256(const AgentArgs* a, int v, int amp_f16, cudaStream_t s, AgentPlanInfo* info);
 
 // Support kernels (support.cu).
 cudaError_t launch_gather_weights(const GatherArgs& g, int ntiles, cudaStream_t s);

@@ -37,24 +37,43 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(const GatherArgs
         else acc[r] = make_float2(0.f, 0.f);
     }
     const int lb = g.tile_ptr[tile], le = g.tile_ptr[tile + 1];
-    for (int li = lb; li < le; ++li) {
-        const int i = __ldg(g.tile_list + li);
-        const int2 o = __ldg(g.offs + i);
-        const int lx = px - o.y;
-        const bool inx = (unsigned)lx < (unsigned)np;
+    // Windows are taken U at a time so that U * RPT loads are in flight per
+    // thread; the accumulation still runs over ascending window index.
+    constexpr int U = 4;
+    for (int li = lb; li < le; li += U) {
+        float wgt[U][RPT];
+        float2 val[U][RPT];
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            const int py = ty0 + grp + r * (kGatherThreads / TW);
-            const int ly = py - o.x;
-            if (inx && (unsigned)ly < (unsigned)np) {
-                const int e = ly * np + lx;
-                const float wgt = __ldg(g.wk + e);
-                if constexpr (MODE == 0) {
-                    acc[r] += (double)wgt;
-                } else {
-                    const float2 s = __ldg(g.src + (size_t)i * P + e);
-                    acc[r].x = fmaf(wgt, s.x, acc[r].x);
-                    acc[r].y = fmaf(wgt, s.y, acc[r].y);
+        for (int k = 0; k < U; ++k) {
+            const bool have = li + k < le;
+            const int i = have ? __ldg(g.tile_list + li + k) : 0;
+            const int2 o = have ? __ldg(g.offs + i) : make_int2(-(1 << 29), -(1 << 29));
+            const int lx = px - o.y;
+            const bool inx = have && (unsigned)lx < (unsigned)np;
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                const int py = ty0 + grp + r * (kGatherThreads / TW);
+                const int ly = py - o.x;
+                wgt[k][r] = 0.f;
+                val[k][r] = make_float2(0.f, 0.f);
+                if (inx && (unsigned)ly < (unsigned)np) {
+                    const int e = ly * np + lx;
+                    wgt[k][r] = __ldg(g.wk + e);
+                    if constexpr (MODE != 0) val[k][r] = __ldg(g.src + (size_t)i * P + e);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                if (wgt[k][r] != 0.f) {
+                    if constexpr (MODE == 0) {
+                        acc[r] += (double)wgt[k][r];
+                    } else {
+                        acc[r].x = fmaf(wgt[k][r], val[k][r].x, acc[r].x);
+                        acc[r].y = fmaf(wgt[k][r], val[k][r].y, acc[r].y);
+                    }
                 }
             }
         }

@@ -44,7 +44,9 @@ class pmace_state_info(ctypes.Structure):
 class pmace_plan(ctypes.Structure):
     _fields_ = [("cluster", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("smem_bytes", ctypes.c_int32), ("tile_h", ctypes.c_int32),
-                ("tile_w", ctypes.c_int32)]
+                ("tile_w", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("cols_per_thread", ctypes.c_int32), ("stage_y", ctypes.c_int32),
+                ("max_clusters", ctypes.c_int32)]
 
 
 EXPORTS = ["pmace_create", "pmace_iterate", "pmace_get_image", "pmace_get_patches",
@@ -202,8 +204,7 @@ def pmace_kernel_times(h, reset=False):
 def pmace_get_plan(h):
     p = pmace_plan()
     _check(_lib.pmace_get_plan(h, ctypes.byref(p)), h)
-    return dict(cluster=p.cluster, threads=p.threads, smem_bytes=p.smem_bytes,
-                tile_h=p.tile_h, tile_w=p.tile_w)
+    return {k: getattr(p, k) for k, _ in pmace_plan._fields_}
 
 
 def pmace_device_bytes(h) -> int:

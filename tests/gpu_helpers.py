@@ -28,17 +28,19 @@ def rounded_inputs(w: datagen.Workload):
 
 
 @contextlib.contextmanager
-def cluster_env(c):
-    old = os.environ.get("PMACE_AGENT_CLUSTER")
-    if c is not None:
-        os.environ["PMACE_AGENT_CLUSTER"] = str(c)
+def plan_env(variant):
+    """Select agent kernel variant `variant` (an index of the per-probe-size
+    plan table) for jobs created inside the block."""
+    old = os.environ.get("PMACE_AGENT_PLAN")
+    if variant is not None:
+        os.environ["PMACE_AGENT_PLAN"] = str(variant)
     try:
         yield
     finally:
         if old is None:
-            os.environ.pop("PMACE_AGENT_CLUSTER", None)
+            os.environ.pop("PMACE_AGENT_PLAN", None)
         else:
-            os.environ["PMACE_AGENT_CLUSTER"] = old
+            os.environ["PMACE_AGENT_PLAN"] = old
 
 
 def random_start(w: datagen.Workload, seed: int = 5) -> np.ndarray:
@@ -53,7 +55,7 @@ def random_start(w: datagen.Workload, seed: int = 5) -> np.ndarray:
 
 
 def run_gpu(w: datagen.Workload, iters: int, alpha: float, rho: float = 0.5, *, kappa=1.25,
-            cluster=None, f16=False, init=None, probe=None, y=None, want_patches=True,
+            variant=None, f16=False, init=None, probe=None, y=None, want_patches=True,
             state=None):
     """Run the CUDA path; returns dict(x_hat, v, r_fp, r_data, plan).
     `state` = (q, xbar, iterations, rho_pending) loads a saved Algorithm 1
@@ -67,7 +69,7 @@ def run_gpu(w: datagen.Workload, iters: int, alpha: float, rho: float = 0.5, *, 
         probe32 = probe.astype(np.complex64)
     if y is not None:
         y32 = y.astype(np.float32)
-    with cluster_env(cluster):
+    with plan_env(variant):
         if f16:
             codes, scales = datagen.quantize_amplitudes_f16(y32.astype(np.float64))
             rec = pm.Reconstruction(probe32, w.offsets, torch.from_numpy(codes).cuda(), w.x.shape,

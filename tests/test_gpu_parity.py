@@ -31,10 +31,10 @@ def _weighted(v, probe):
     return v * np.abs(probe)[None]
 
 
-def _check_iteration(w, iters=1, alpha=0.5, rho=0.5, cluster=None, f16=False, tol=TOL_ITER):
+def _check_iteration(w, iters=1, alpha=0.5, rho=0.5, variant=None, f16=False, tol=TOL_ITER):
     """Iterations from a well-conditioned random start (see random_start)."""
     x0 = random_start(w)
-    g = run_gpu(w, iters, alpha, rho, cluster=cluster, f16=f16, init=x0)
+    g = run_gpu(w, iters, alpha, rho, variant=variant, f16=f16, init=x0)
     o = run_oracle(w, iters, alpha, rho, f16=f16, x0=x0)
     e_img = rel_l2(g["x_hat"], o["x_hat"])
     e_vw = rel_l2(_weighted(g["v"], w.probe), _weighted(o["v"], w.probe))
@@ -57,29 +57,39 @@ def test_five_iterations_small():
     assert abs(g["r_data"] - o["r_data"]) < 1e-4 * o["r_data"]
 
 
-@pytest.mark.parametrize("cluster", [1, 2])
-def test_one_iteration_np64(cluster):
+VARIANTS = [0, 1, 2, 3]   # every compiled agent kernel variant of a probe size
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_one_iteration_np32(variant):
+    w = datagen.make_workload("small", seed=17)
+    g, _ = _check_iteration(w, 1, variant=variant)
+    assert g["plan"]["variant"] == variant
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_one_iteration_np64(variant):
     w = datagen.make_workload(dict(MID64, name="mid64"), seed=3)
-    g, _ = _check_iteration(w, 1, cluster=cluster)
-    assert g["plan"]["cluster"] == cluster
+    g, _ = _check_iteration(w, 1, variant=variant)
+    assert g["plan"]["variant"] == variant
 
 
-@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
-def test_one_iteration_np128(cluster):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_one_iteration_np128(variant):
     w = datagen.make_workload(dict(MID128, name="mid128"), seed=4)
-    g, _ = _check_iteration(w, 1, cluster=cluster)
-    assert g["plan"]["cluster"] == cluster
+    g, _ = _check_iteration(w, 1, variant=variant)
+    assert g["plan"]["variant"] == variant
 
 
-@pytest.mark.parametrize("cluster", [4, 8])
-def test_one_iteration_np256_full_config(cluster):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_one_iteration_np256_full_config(variant):
     """The 600 x 600 / 256 x 256 / 324-window workload at full size."""
     w = datagen.make_workload("p256", seed=1)
-    g, _ = _check_iteration(w, 1, cluster=cluster)
-    assert g["plan"]["cluster"] == cluster
+    g, _ = _check_iteration(w, 1, variant=variant)
+    assert g["plan"]["variant"] == variant
 
 
-def _midrun_step(w, k, alpha=0.5, rho=0.5, cluster=None):
+def _midrun_step(w, k, alpha=0.5, rho=0.5, variant=None):
     """One iteration from the FP64 oracle's state after k iterations from the
     energy-matched constant start (loaded through the checkpoint call)."""
     from oracle import pmace_oracle as orc
@@ -89,7 +99,7 @@ def _midrun_step(w, k, alpha=0.5, rho=0.5, cluster=None):
     xb = xb.astype(np.complex64).astype(np.complex128)
     z = orc.redistribute(xb, w.offsets, w.np_)
     o = run_oracle(w, 1, alpha, rho, v0=q + 2 * rho * z, z_prev=z)
-    g = run_gpu(w, 1, alpha, rho, cluster=cluster, state=(q, xb, k, rho))
+    g = run_gpu(w, 1, alpha, rho, variant=variant, state=(q, xb, k, rho))
     e_img = rel_l2(g["x_hat"], o["x_hat"])
     e_vw = rel_l2(_weighted(g["v"], w.probe), _weighted(o["v"], w.probe))
     print(f"{w.name} np={w.np_} mid-run k={k} plan={g['plan']}: x_hat {e_img:.2e}  |d|v {e_vw:.2e}"
@@ -107,9 +117,9 @@ def test_midrun_iteration_np128():
     _midrun_step(datagen.make_workload(dict(MID128, name="mid128"), seed=15), 5)
 
 
-@pytest.mark.parametrize("cluster", [4, 8])
-def test_midrun_iteration_np256_full_config(cluster):
-    _midrun_step(datagen.make_workload("p256", seed=3), 3, cluster=cluster)
+@pytest.mark.parametrize("variant", [0, 2])
+def test_midrun_iteration_np256_full_config(variant):
+    _midrun_step(datagen.make_workload("p256", seed=3), 3, variant=variant)
 
 
 def test_nrmse_from_constant_start_np128():
