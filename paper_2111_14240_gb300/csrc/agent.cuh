@@ -37,19 +37,20 @@ namespace pmace {
 
 namespace cg = cooperative_groups;
 
-// Geometry of one plan: N x N probe, C CTAs per patch, CPT columns per
+// Geometry of one plan: N x N probe, C CTAs per window, CPT columns per
 // thread in the column step (N / CPT threads per CTA), YST = 1 to stage the
 // amplitude rows in shared memory with asynchronous copies at kernel start
-// (0: the column step loads them itself).
-template <int N, int C, int CPT, int YST, int AMP>
+// (0: the column step loads them itself), PPC windows per cluster (every
+// barrier then serves PPC windows).
+template <int N, int C, int CPT, int YST, int PPC, int AMP>
 struct AgentGeom {
     static constexpr int R = N / C;                 // rows per CTA = column DFT length
     static constexpr int RS = TileGeom<N>::RS;
     static constexpr int kThreads = N / CPT;
     static constexpr int kWarps = kThreads / 32;
-    static constexpr int kTileBytes = R * RS * (int)sizeof(float2);
+    static constexpr int kTileBytes = PPC * R * RS * (int)sizeof(float2);
     static constexpr int kTwBytes = N * (int)sizeof(float2);
-    static constexpr int kYBytes = YST ? R * N * (AMP ? 2 : 4) : 0;
+    static constexpr int kYBytes = YST ? PPC * R * N * (AMP ? 2 : 4) : 0;
     static constexpr int kSmem = kTileBytes + kTwBytes + kYBytes;
     static constexpr RadixPlan kRow = radix_plan(N);
     // resident CTAs per SM the shared memory allows (228 KB per SM, 1 KB
@@ -127,74 +128,92 @@ __device__ __forceinline__ void for_pairs(F&& f) {
 }
 
 // MINB: resident CTAs per SM the register allocation is sized for.
-template <int N, int C, int CPT, int YST, int AMP, int MINB>
-__global__ void __launch_bounds__(AgentGeom<N, C, CPT, YST, AMP>::kThreads, MINB)
+template <int N, int C, int CPT, int YST, int PPC, int AMP, int MINB>
+__global__ void __launch_bounds__(AgentGeom<N, C, CPT, YST, PPC, AMP>::kThreads, MINB)
 agent_kernel(const AgentArgs a) {
-    using G = AgentGeom<N, C, CPT, YST, AMP>;
+    using G = AgentGeom<N, C, CPT, YST, PPC, AMP>;
     constexpr int R = G::R, RS = G::RS, T = G::kThreads, NW = G::kWarps;
     constexpr int r1 = G::kRow.first, r2 = G::kRow.second;
     constexpr int S1 = N / r1;
     constexpr int HALF = N / 2;
     constexpr int BATCH = 4;
+    constexpr int ROWS = PPC * R;                  // tile rows: PPC windows of R rows
     static_assert(r2 > 1, "row transform needs two stages");
     static_assert(R == 16 || R == 32, "column DFT length must be 16 or 32");
     static_assert(C == 1 || R % C == 0, "cross-CTA stage needs C | rows per CTA");
 
     extern __shared__ float4 smem_raw[];
     float2* tile = reinterpret_cast<float2*>(smem_raw);
-    float2* tw = tile + R * RS;
+    float2* tw = tile + ROWS * RS;
     char* ybuf = reinterpret_cast<char*>(tw + N);
     __shared__ double red[(T / 32) * 4];
 
     int rank = 0;
     if constexpr (C > 1) rank = (int)cg::this_cluster().block_rank();
-    const int j = blockIdx.x / C;
-    const size_t pbase = ((size_t)j * N + (size_t)rank * R) * N;   // first element of my rows
+    const int j0 = (blockIdx.x / C) * PPC;         // first window of this cluster
+
+    // window p of the cluster: j0 + p; it may lie past the end (J not a
+    // multiple of PPC), in which case its rows are computed on zeros and
+    // nothing of it is loaded or stored
+    auto valid = [&](int p) { return j0 + p < a.J; };
+    auto pbase_of = [&](int p) { return ((size_t)(j0 + p) * N + (size_t)rank * R) * N; };
 
     // ---- amplitude rows of this CTA -> shared memory, asynchronously
     if constexpr (YST) {
-        constexpr int CH = G::kYBytes / 16;
-        const char* ysrc = static_cast<const char*>(a.y) + pbase * (AMP ? 2 : 4);
-        for (int c = threadIdx.x; c < CH; c += T) cp_async16(ybuf + 16 * c, ysrc + 16 * c);
+        constexpr int CH = G::kYBytes / PPC / 16;
+#pragma unroll
+        for (int p = 0; p < PPC; ++p) {
+            if (!valid(p)) continue;
+            const char* ysrc = static_cast<const char*>(a.y) + pbase_of(p) * (AMP ? 2 : 4);
+            char* ydst = ybuf + p * (G::kYBytes / PPC);
+            for (int c = threadIdx.x; c < CH; c += T) cp_async16(ydst + 16 * c, ysrc + 16 * c);
+        }
         cp_async_commit();
     }
     for (int i = threadIdx.x; i < N; i += T) tw[i] = a.tw[i];
-    const int2 off = a.offs[j];
-    float2* qp = a.q + pbase;   // read (S0) and overwritten (S5) pair by pair by one thread
-    float2* __restrict__ uo = a.u + pbase;
-    const float2* __restrict__ xb = a.xbar + (size_t)(off.x + rank * R) * a.n2 + off.y;
     const float2* __restrict__ pr = a.probe + (size_t)rank * R * N;
     const float2* __restrict__ di = a.dinv + (size_t)rank * R * N;
     const float two_rho_prev = 2.0f * a.rho_prev;
 
     // ---- S0 + S1: a = d . (q + 2 rho_prev xbar) into the tile, natural order
-    for_pairs<N, R, T, BATCH>([&](int i0) {
-        float4 qv[BATCH], dv[BATCH];
-        float2 x0[BATCH], x1[BATCH];
 #pragma unroll
-        for (int i = 0; i < BATCH; ++i) {
-            const int t = threadIdx.x + (i0 + i) * T;
-            const int row = t / HALF, c = 2 * (t % HALF);
-            qv[i] = *reinterpret_cast<const float4*>(qp + row * N + c);
-            dv[i] = __ldg(reinterpret_cast<const float4*>(pr + row * N + c));
-            x0[i] = __ldg(xb + (size_t)row * a.n2 + c);
-            x1[i] = __ldg(xb + (size_t)row * a.n2 + c + 1);
+    for (int p = 0; p < PPC; ++p) {
+        float2* tp = tile + p * R * RS;
+        if (!valid(p)) {
+            for (int e = threadIdx.x; e < R * RS; e += T) tp[e] = make_float2(0.f, 0.f);
+            continue;
         }
+        const int2 off = a.offs[j0 + p];
+        const float2* qp = a.q + pbase_of(p);
+        const float2* __restrict__ xb = a.xbar + (size_t)(off.x + rank * R) * a.n2 + off.y;
+        for_pairs<N, R, T, BATCH>([&](int i0) {
+            float4 qv[BATCH], dv[BATCH];
+            float2 x0[BATCH], x1[BATCH];
 #pragma unroll
-        for (int i = 0; i < BATCH; ++i) {
-            const int t = threadIdx.x + (i0 + i) * T;
-            const int row = t / HALF, c = 2 * (t % HALF);
-            const float2 v0 = make_float2(fmaf(two_rho_prev, x0[i].x, qv[i].x), fmaf(two_rho_prev, x0[i].y, qv[i].y));
-            const float2 v1 = make_float2(fmaf(two_rho_prev, x1[i].x, qv[i].z), fmaf(two_rho_prev, x1[i].y, qv[i].w));
-            float2* dst = tile + row * RS + pcol(c);
-            dst[0] = cmul(make_float2(dv[i].x, dv[i].y), v0);
-            dst[1] = cmul(make_float2(dv[i].z, dv[i].w), v1);
-        }
-    });
+            for (int i = 0; i < BATCH; ++i) {
+                const int t = threadIdx.x + (i0 + i) * T;
+                const int row = t / HALF, c = 2 * (t % HALF);
+                qv[i] = *reinterpret_cast<const float4*>(qp + row * N + c);
+                dv[i] = __ldg(reinterpret_cast<const float4*>(pr + row * N + c));
+                x0[i] = __ldg(xb + (size_t)row * a.n2 + c);
+                x1[i] = __ldg(xb + (size_t)row * a.n2 + c + 1);
+            }
+#pragma unroll
+            for (int i = 0; i < BATCH; ++i) {
+                const int t = threadIdx.x + (i0 + i) * T;
+                const int row = t / HALF, c = 2 * (t % HALF);
+                const float2 v0 = make_float2(fmaf(two_rho_prev, x0[i].x, qv[i].x), fmaf(two_rho_prev, x0[i].y, qv[i].y));
+                const float2 v1 = make_float2(fmaf(two_rho_prev, x1[i].x, qv[i].z), fmaf(two_rho_prev, x1[i].y, qv[i].w));
+                float2* dst = tp + row * RS + pcol(c);
+                dst[0] = cmul(make_float2(dv[i].x, dv[i].y), v0);
+                dst[1] = cmul(make_float2(dv[i].z, dv[i].w), v1);
+            }
+        });
+    }
     __syncthreads();
 
     // ---- row DIF: span N (radix r1), then span r2, on the warp's own rows
-    for_warp_rows<N, R, NW, r1>([&](int row, int b) {
+    for_warp_rows<N, ROWS, NW, r1>([&](int row, int b) {
         float2* rp = tile + row * RS;
         float2 x[r1];
 #pragma unroll
@@ -206,7 +225,7 @@ agent_kernel(const AgentArgs a) {
         for (int k = 0; k < r1; ++k) rp[pcol(b + k * S1)] = x[k];
     });
     __syncwarp();
-    for_warp_rows<N, R, NW, r2>([&](int row, int m) {
+    for_warp_rows<N, ROWS, NW, r2>([&](int row, int m) {
         float2* rp = tile + row * RS;
         float2 x[r2];
 #pragma unroll
@@ -220,82 +239,89 @@ agent_kernel(const AgentArgs a) {
     if constexpr (C > 1) {
         cg::cluster_group cl = cg::this_cluster();
         cl.sync();
-        cross_stage<N, R, C, false, T>(tile, tw, rank);
-        cp_async_wait_all();
+        cross_stage<N, ROWS, R, C, false, T>(tile, tw, rank);
+        if constexpr (YST) cp_async_wait_all();
         cl.sync();
     } else {
-        cp_async_wait_all();
+        if constexpr (YST) cp_async_wait_all();
         __syncthreads();
     }
 
     // ---- R-point column DFT in registers + S3 + inverse R-point DFT.
     // Thread `col` (CPT columns per thread) holds local rows 0..R-1 of its
-    // column; after the forward
-    // DFT register k2 holds frequency row rank + C*k2, which is where the
-    // amplitudes were stored (kernel order: row rank*R + k2).
-    float acc_d = 0.f, acc_y = 0.f;
-    float yscale = 1.0f;
-    if constexpr (AMP == 1) yscale = __ldg(a.yscale + j);
+    // column of window p; after the forward DFT register k2 holds frequency
+    // row rank + C*k2, which is where the amplitudes were stored (kernel
+    // order: row rank*R + k2).
+    float acc_d[PPC], acc_y[PPC];
+#pragma unroll
+    for (int p = 0; p < PPC; ++p) {
+        acc_d[p] = 0.f;
+        acc_y[p] = 0.f;
+        float yscale = 1.0f;
+        if constexpr (AMP == 1) yscale = valid(p) ? __ldg(a.yscale + j0 + p) : 0.f;
+        const size_t pb = pbase_of(p);
 #pragma unroll 1
-    for (int ci = 0; ci < CPT; ++ci) {
-        const int col = threadIdx.x + ci * T;
-        float yv[R];
+        for (int ci = 0; ci < CPT; ++ci) {
+            const int col = threadIdx.x + ci * T;
+            float yv[R];
 #pragma unroll
-        for (int k = 0; k < R; ++k) {
-            if constexpr (YST) {
-                if constexpr (AMP == 0) yv[k] = reinterpret_cast<const float*>(ybuf)[k * N + col];
-                else yv[k] = __half2float(reinterpret_cast<const __half*>(ybuf)[k * N + col]) * yscale;
-            } else {
-                yv[k] = load_amp<AMP>(a.y, pbase + (size_t)k * N + col, yscale);
+            for (int k = 0; k < R; ++k) {
+                if constexpr (YST) {
+                    const char* yb = ybuf + p * (G::kYBytes / PPC);
+                    if constexpr (AMP == 0) yv[k] = reinterpret_cast<const float*>(yb)[k * N + col];
+                    else yv[k] = __half2float(reinterpret_cast<const __half*>(yb)[k * N + col]) * yscale;
+                } else {
+                    yv[k] = valid(p) ? load_amp<AMP>(a.y, pb + (size_t)k * N + col, yscale) : 0.f;
+                }
             }
+            float2* cp = tile + p * R * RS + pcol(col);
+            float2 x[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) x[k] = cp[k * RS];
+            Dft<R, false>::run(x);
+            const float inv_n = 1.0f / (float)N;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                // phase A/|A| (0 only where A = 0); coefficients whose squared
+                // magnitude would underflow are rescaled by 2^100 first
+                float2 xa = x[k];
+                float m2 = fmaf(xa.x, xa.x, xa.y * xa.y);
+                float unscale = inv_n;
+                if (m2 < 0x1p-100f) {
+                    xa = xa * 0x1p100f;
+                    m2 = fmaf(xa.x, xa.x, xa.y * xa.y);
+                    unscale = inv_n * 0x1p-100f;
+                }
+                float2 o = make_float2(0.f, 0.f);
+                float mag = 0.f;
+                if (m2 > 0.f) {
+                    const float rs = rsqrtf(m2);
+                    mag = m2 * rs * unscale;
+                    o = xa * (yv[k] * rs);
+                }
+                const float e = yv[k] - mag;
+                acc_d[p] = fmaf(e, e, acc_d[p]);
+                acc_y[p] = fmaf(yv[k], yv[k], acc_y[p]);
+                x[k] = o;
+            }
+            Dft<R, true>::run(x);
+#pragma unroll
+            for (int k = 0; k < R; ++k) cp[k * RS] = x[k];
         }
-        float2* cp = tile + pcol(col);
-        float2 x[R];
-#pragma unroll
-        for (int k = 0; k < R; ++k) x[k] = cp[k * RS];
-        Dft<R, false>::run(x);
-        const float inv_n = 1.0f / (float)N;
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            // phase A/|A| (0 only where A = 0); coefficients whose squared
-            // magnitude would underflow are rescaled by 2^100 first
-            float2 xa = x[k];
-            float m2 = fmaf(xa.x, xa.x, xa.y * xa.y);
-            float unscale = inv_n;
-            if (m2 < 0x1p-100f) {
-                xa = xa * 0x1p100f;
-                m2 = fmaf(xa.x, xa.x, xa.y * xa.y);
-                unscale = inv_n * 0x1p-100f;
-            }
-            float2 o = make_float2(0.f, 0.f);
-            float mag = 0.f;
-            if (m2 > 0.f) {
-                const float rs = rsqrtf(m2);
-                mag = m2 * rs * unscale;
-                o = xa * (yv[k] * rs);
-            }
-            const float e = yv[k] - mag;
-            acc_d = fmaf(e, e, acc_d);
-            acc_y = fmaf(yv[k], yv[k], acc_y);
-            x[k] = o;
-        }
-        Dft<R, true>::run(x);
-#pragma unroll
-        for (int k = 0; k < R; ++k) cp[k * RS] = x[k];
     }
 
     // ---- column DIT, cross-CTA stage
     if constexpr (C > 1) {
         cg::cluster_group cl = cg::this_cluster();
         cl.sync();
-        cross_stage<N, R, C, true, T>(tile, tw, rank);
+        cross_stage<N, ROWS, R, C, true, T>(tile, tw, rank);
         cl.sync();   // also keeps every tile alive until the peers are done with it
     } else {
         __syncthreads();
     }
 
     // ---- row DIT: span r2, then span N; result back in the tile, natural order
-    for_warp_rows<N, R, NW, r2>([&](int row, int m) {
+    for_warp_rows<N, ROWS, NW, r2>([&](int row, int m) {
         float2* rp = tile + row * RS;
         float2 x[r2];
 #pragma unroll
@@ -305,7 +331,7 @@ agent_kernel(const AgentArgs a) {
         for (int k = 0; k < r2; ++k) rp[pcol(m * r2 + k)] = x[k];
     });
     __syncwarp();
-    for_warp_rows<N, R, NW, r1>([&](int row, int b) {
+    for_warp_rows<N, ROWS, NW, r1>([&](int row, int b) {
         float2* rp = tile + row * RS;
         float2 x[r1];
 #pragma unroll
@@ -319,62 +345,80 @@ agent_kernel(const AgentArgs a) {
     __syncthreads();
 
     // ---- S4 + S5, pair by pair
-    float acc_z = 0.f, acc_w = 0.f;
+    float acc_z[PPC], acc_w[PPC];
     {
         const float scale = 1.0f / (float)N;          // orthonormal F^*
         const float inv1pa = 1.0f / (1.0f + a.alpha);
         const float alpha = a.alpha;
         const float two_rho = 2.0f * a.rho_cur;
         const bool first = a.first != 0;
-        auto agent_update = [&](float2 g, float2 q, float2 xv, float2 dv, float2& u, float2& qn) {
-            const float2 v = make_float2(fmaf(two_rho_prev, xv.x, q.x), fmaf(two_rho_prev, xv.y, q.y));
-            float2 w;
-            if (dv.x == 0.f && dv.y == 0.f) {
-                w = v;                                    // d treated as absent here
-            } else {
-                const float2 h = cmul(dv, g * scale);     // D^-1 F^* A'
-                w = make_float2(fmaf(alpha, v.x, h.x) * inv1pa, fmaf(alpha, v.y, h.y) * inv1pa);
-            }
-            u = make_float2(2.f * w.x - v.x, 2.f * w.y - v.y);
-            qn = make_float2(fmaf(-two_rho, w.x, v.x), fmaf(-two_rho, w.y, v.y));
-            const float2 z = first ? v : xv;
-            const float dzx = z.x - w.x, dzy = z.y - w.y;
-            acc_z = fmaf(dzx, dzx, fmaf(dzy, dzy, acc_z));
-            acc_w = fmaf(w.x, w.x, fmaf(w.y, w.y, acc_w));
-        };
-        for_pairs<N, R, T, BATCH>([&](int i0) {
-            float4 qv[BATCH], dv[BATCH];
-            float2 x0[BATCH], x1[BATCH];
 #pragma unroll
-            for (int i = 0; i < BATCH; ++i) {
-                const int t = threadIdx.x + (i0 + i) * T;
-                const int row = t / HALF, c = 2 * (t % HALF);
-                qv[i] = *reinterpret_cast<const float4*>(qp + row * N + c);
-                dv[i] = __ldg(reinterpret_cast<const float4*>(di + row * N + c));
-                x0[i] = __ldg(xb + (size_t)row * a.n2 + c);
-                x1[i] = __ldg(xb + (size_t)row * a.n2 + c + 1);
-            }
+        for (int p = 0; p < PPC; ++p) {
+            float az = 0.f, aw = 0.f;
+            auto agent_update = [&](float2 g, float2 q, float2 xv, float2 dv, float2& u, float2& qn) {
+                const float2 v = make_float2(fmaf(two_rho_prev, xv.x, q.x), fmaf(two_rho_prev, xv.y, q.y));
+                float2 w;
+                if (dv.x == 0.f && dv.y == 0.f) {
+                    w = v;                                    // d treated as absent here
+                } else {
+                    const float2 h = cmul(dv, g * scale);     // D^-1 F^* A'
+                    w = make_float2(fmaf(alpha, v.x, h.x) * inv1pa, fmaf(alpha, v.y, h.y) * inv1pa);
+                }
+                u = make_float2(2.f * w.x - v.x, 2.f * w.y - v.y);
+                qn = make_float2(fmaf(-two_rho, w.x, v.x), fmaf(-two_rho, w.y, v.y));
+                const float2 z = first ? v : xv;
+                const float dzx = z.x - w.x, dzy = z.y - w.y;
+                az = fmaf(dzx, dzx, fmaf(dzy, dzy, az));
+                aw = fmaf(w.x, w.x, fmaf(w.y, w.y, aw));
+            };
+            if (valid(p)) {
+                const int2 off = a.offs[j0 + p];
+                float2* qp = a.q + pbase_of(p);   // read (S0) and overwritten (S5) pair by pair by one thread
+                float2* __restrict__ uo = a.u + pbase_of(p);
+                const float2* __restrict__ xb = a.xbar + (size_t)(off.x + rank * R) * a.n2 + off.y;
+                const float2* tp = tile + p * R * RS;
+                for_pairs<N, R, T, BATCH>([&](int i0) {
+                    float4 qv[BATCH], dv[BATCH];
+                    float2 x0[BATCH], x1[BATCH];
 #pragma unroll
-            for (int i = 0; i < BATCH; ++i) {
-                const int t = threadIdx.x + (i0 + i) * T;
-                const int row = t / HALF, c = 2 * (t % HALF);
-                const float2* src = tile + row * RS + pcol(c);
-                float2 u0, u1, q0, q1;
-                agent_update(src[0], make_float2(qv[i].x, qv[i].y), x0[i], make_float2(dv[i].x, dv[i].y), u0, q0);
-                agent_update(src[1], make_float2(qv[i].z, qv[i].w), x1[i], make_float2(dv[i].z, dv[i].w), u1, q1);
-                *reinterpret_cast<float4*>(uo + row * N + c) = make_float4(u0.x, u0.y, u1.x, u1.y);
-                *reinterpret_cast<float4*>(qp + row * N + c) = make_float4(q0.x, q0.y, q1.x, q1.y);
+                    for (int i = 0; i < BATCH; ++i) {
+                        const int t = threadIdx.x + (i0 + i) * T;
+                        const int row = t / HALF, c = 2 * (t % HALF);
+                        qv[i] = *reinterpret_cast<const float4*>(qp + row * N + c);
+                        dv[i] = __ldg(reinterpret_cast<const float4*>(di + row * N + c));
+                        x0[i] = __ldg(xb + (size_t)row * a.n2 + c);
+                        x1[i] = __ldg(xb + (size_t)row * a.n2 + c + 1);
+                    }
+#pragma unroll
+                    for (int i = 0; i < BATCH; ++i) {
+                        const int t = threadIdx.x + (i0 + i) * T;
+                        const int row = t / HALF, c = 2 * (t % HALF);
+                        const float2* src = tp + row * RS + pcol(c);
+                        float2 u0, u1, q0, q1;
+                        agent_update(src[0], make_float2(qv[i].x, qv[i].y), x0[i], make_float2(dv[i].x, dv[i].y), u0, q0);
+                        agent_update(src[1], make_float2(qv[i].z, qv[i].w), x1[i], make_float2(dv[i].z, dv[i].w), u1, q1);
+                        *reinterpret_cast<float4*>(uo + row * N + c) = make_float4(u0.x, u0.y, u1.x, u1.y);
+                        *reinterpret_cast<float4*>(qp + row * N + c) = make_float4(q0.x, q0.y, q1.x, q1.y);
+                    }
+                });
             }
-        });
+            acc_z[p] = az;
+            acc_w[p] = aw;
+        }
     }
-    float acc[4] = {acc_z, acc_w, acc_d, acc_y};
-    block_reduce4<T>(acc, red, a.partials + ((size_t)j * C + rank) * 4);
+#pragma unroll
+    for (int p = 0; p < PPC; ++p) {
+        float acc[4] = {acc_z[p], acc_w[p], acc_d[p], acc_y[p]};
+        if (p > 0) __syncthreads();   // the reduction buffer is reused
+        if (valid(p)) block_reduce4<T>(acc, red, a.partials + ((size_t)(j0 + p) * C + rank) * 4);
+        else __syncthreads();         // keep the barrier count uniform
+    }
 }
 
-template <int N, int C, int CPT, int YST, int AMP, int MINB>
+template <int N, int C, int CPT, int YST, int PPC, int AMP, int MINB>
 cudaError_t launch_agent_impl(const AgentArgs& a, cudaStream_t s) {
-    using G = AgentGeom<N, C, CPT, YST, AMP>;
-    void (*fn)(const AgentArgs) = agent_kernel<N, C, CPT, YST, AMP, MINB>;
+    using G = AgentGeom<N, C, CPT, YST, PPC, AMP>;
+    void (*fn)(const AgentArgs) = agent_kernel<N, C, CPT, YST, PPC, AMP, MINB>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem);
     if (e != cudaSuccess) return e;
     if constexpr (C > 1) {
@@ -382,7 +426,7 @@ cudaError_t launch_agent_impl(const AgentArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(a.J * C), 1, 1);
+    cfg.gridDim = dim3((unsigned)(((a.J + PPC - 1) / PPC) * C), 1, 1);
     cfg.blockDim = dim3(G::kThreads, 1, 1);
     cfg.dynamicSmemBytes = G::kSmem;
     cfg.stream = s;
@@ -397,10 +441,10 @@ cudaError_t launch_agent_impl(const AgentArgs& a, cudaStream_t s) {
 }
 
 // How many clusters of this plan the device holds at once (0: not launchable).
-template <int N, int C, int CPT, int YST, int AMP, int MINB>
+template <int N, int C, int CPT, int YST, int PPC, int AMP, int MINB>
 int plan_max_clusters_impl() {
-    using G = AgentGeom<N, C, CPT, YST, AMP>;
-    void (*fn)(const AgentArgs) = agent_kernel<N, C, CPT, YST, AMP, MINB>;
+    using G = AgentGeom<N, C, CPT, YST, PPC, AMP>;
+    void (*fn)(const AgentArgs) = agent_kernel<N, C, CPT, YST, PPC, AMP, MINB>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -439,28 +483,28 @@ int plan_max_clusters_impl() {
 }
 
 // One plan: query (a == nullptr) or launch, for either amplitude format.
-template <int N, int C, int CPT, int YST>
+template <int N, int C, int CPT, int YST, int PPC>
 cudaError_t agent_variant(const AgentArgs* a, int amp_f16, cudaStream_t s, AgentPlanInfo* info) {
     if (amp_f16) {
-        using G = AgentGeom<N, C, CPT, YST, 1>;
+        using G = AgentGeom<N, C, CPT, YST, PPC, 1>;
         if (a == nullptr) {
             info->threads = G::kThreads;
             info->smem_bytes = G::kSmem;
-            info->max_clusters = plan_max_clusters_impl<N, C, CPT, YST, 1, G::kMinBlocks>();
+            info->max_clusters = plan_max_clusters_impl<N, C, CPT, YST, PPC, 1, G::kMinBlocks>();
             info->launchable = info->max_clusters > 0;
             return cudaSuccess;
         }
-        return launch_agent_impl<N, C, CPT, YST, 1, G::kMinBlocks>(*a, s);
+        return launch_agent_impl<N, C, CPT, YST, PPC, 1, G::kMinBlocks>(*a, s);
     }
-    using G = AgentGeom<N, C, CPT, YST, 0>;
+    using G = AgentGeom<N, C, CPT, YST, PPC, 0>;
     if (a == nullptr) {
         info->threads = G::kThreads;
         info->smem_bytes = G::kSmem;
-        info->max_clusters = plan_max_clusters_impl<N, C, CPT, YST, 0, G::kMinBlocks>();
+        info->max_clusters = plan_max_clusters_impl<N, C, CPT, YST, PPC, 0, G::kMinBlocks>();
         info->launchable = info->max_clusters > 0;
         return cudaSuccess;
     }
-    return launch_agent_impl<N, C, CPT, YST, 0, G::kMinBlocks>(*a, s);
+    return launch_agent_impl<N, C, CPT, YST, PPC, 0, G::kMinBlocks>(*a, s);
 }
 
 }  // namespace pmace

@@ -4,17 +4,25 @@
 
 namespace pmace {
 
-static_assert(agent_variant_of(32, 0).cluster == 2 && agent_variant_of(32, 0).cols_per_thread == 1 && agent_variant_of(32, 0).stage_y == 1, "variant table mismatch");
-static_assert(agent_variant_of(32, 1).cluster == 1 && agent_variant_of(32, 1).cols_per_thread == 1 && agent_variant_of(32, 1).stage_y == 1, "variant table mismatch");
-static_assert(agent_variant_of(32, 2).cluster == 2 && agent_variant_of(32, 2).cols_per_thread == 1 && agent_variant_of(32, 2).stage_y == 0, "variant table mismatch");
-static_assert(agent_variant_of(32, 3).cluster == 1 && agent_variant_of(32, 3).cols_per_thread == 1 && agent_variant_of(32, 3).stage_y == 0, "variant table mismatch");
+static_assert(agent_variant_of(32, 0).cluster == 2 && agent_variant_of(32, 0).cols_per_thread == 1 &&
+              agent_variant_of(32, 0).stage_y == 1 && agent_variant_of(32, 0).windows == 1,
+              "variant table mismatch");
+static_assert(agent_variant_of(32, 1).cluster == 1 && agent_variant_of(32, 1).cols_per_thread == 1 &&
+              agent_variant_of(32, 1).stage_y == 1 && agent_variant_of(32, 1).windows == 1,
+              "variant table mismatch");
+static_assert(agent_variant_of(32, 2).cluster == 2 && agent_variant_of(32, 2).cols_per_thread == 1 &&
+              agent_variant_of(32, 2).stage_y == 0 && agent_variant_of(32, 2).windows == 2,
+              "variant table mismatch");
+static_assert(agent_variant_of(32, 3).cluster == 1 && agent_variant_of(32, 3).cols_per_thread == 1 &&
+              agent_variant_of(32, 3).stage_y == 0 && agent_variant_of(32, 3).windows == 1,
+              "variant table mismatch");
 
 cudaError_t agent_entry_32(const AgentArgs* a, int v, int amp_f16, cudaStream_t s, AgentPlanInfo* info) {
     switch (v) {
-        case 0: return agent_variant<32, 2, 1, 1>(a, amp_f16, s, info);
-        case 1: return agent_variant<32, 1, 1, 1>(a, amp_f16, s, info);
-        case 2: return agent_variant<32, 2, 1, 0>(a, amp_f16, s, info);
-        case 3: return agent_variant<32, 1, 1, 0>(a, amp_f16, s, info);
+        case 0: return agent_variant<32, 2, 1, 1, 1>(a, amp_f16, s, info);
+        case 1: return agent_variant<32, 1, 1, 1, 1>(a, amp_f16, s, info);
+        case 2: return agent_variant<32, 2, 1, 0, 2>(a, amp_f16, s, info);
+        case 3: return agent_variant<32, 1, 1, 0, 1>(a, amp_f16, s, info);
         default: return cudaErrorInvalidValue;
     }
 }

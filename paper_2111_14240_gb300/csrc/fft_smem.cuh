@@ -180,30 +180,48 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
 // shared memory; a butterfly's elements are read and written by one thread
 // only, so the stage is in place without staging.  `tile` is this CTA's
 // tile; the peers' copies are addressed through mapa.
-template <int N, int NROWS, int C, bool INV, int T>
+// The tile may hold several windows of WR rows each (NROWS = windows * WR);
+// the twiddle of local row b is that of row b % WR of its window.
+template <int N, int NROWS, int WR, int C, bool INV, int T>
 __device__ __forceinline__ void cross_stage(const float2* tile, const float2* __restrict__ tw, int rank) {
-    const uint32_t mine = smem_addr(tile);
     constexpr int RS = TileGeom<N>::RS;
-    constexpr int BR = NROWS / C;     // butterfly rows per CTA
-    constexpr int NB = BR * N;
-    for (int t = threadIdx.x; t < NB; t += T) {
-        const int col = t % N;
-        const int b = rank * BR + t / N;
-        const uint32_t off = (uint32_t)(b * RS + pcol(col)) * (uint32_t)sizeof(float2);
-        float2 x[C];
+    constexpr int BR = NROWS / C;         // butterfly rows per CTA
+    constexpr int NB = BR * N;            // butterflies per CTA
+    static_assert(NB % T == 0, "butterflies must split evenly over threads");
+    constexpr int PER = NB / T;           // butterflies per thread
+    // butterflies whose remote loads are issued together (up to 16 values in flight)
+    constexpr int BB = (16 / C) < PER ? (16 / C > 0 ? 16 / C : 1) : PER;
+    static_assert(PER % BB == 0, "butterfly batches must divide the per-thread count");
+    const uint32_t mine = smem_addr(tile);
+#pragma unroll 1
+    for (int p0 = 0; p0 < PER; p0 += BB) {
+        float2 x[BB][C];
+        uint32_t off[BB];
+        int bidx[BB];
 #pragma unroll
-        for (int k = 0; k < C; ++k) x[k] = ld_cluster(cluster_addr(mine + off, (uint32_t)k));
-        if constexpr (INV) {
+        for (int i = 0; i < BB; ++i) {
+            const int t = threadIdx.x + (p0 + i) * T;
+            const int col = t % N;
+            bidx[i] = rank * BR + t / N;
+            off[i] = (uint32_t)(bidx[i] * RS + pcol(col)) * (uint32_t)sizeof(float2);
 #pragma unroll
-            for (int k = 1; k < C; ++k) x[k] = cmulc(x[k], tw[b * k]);
-            Dft<C, true>::run(x);
-        } else {
-            Dft<C, false>::run(x);
-#pragma unroll
-            for (int k = 1; k < C; ++k) x[k] = cmul(x[k], tw[b * k]);
+            for (int k = 0; k < C; ++k) x[i][k] = ld_cluster(cluster_addr(mine + off[i], (uint32_t)k));
         }
 #pragma unroll
-        for (int k = 0; k < C; ++k) st_cluster(cluster_addr(mine + off, (uint32_t)k), x[k]);
+        for (int i = 0; i < BB; ++i) {
+            const int b = bidx[i] % WR;
+            if constexpr (INV) {
+#pragma unroll
+                for (int k = 1; k < C; ++k) x[i][k] = cmulc(x[i][k], tw[b * k]);
+                Dft<C, true>::run(x[i]);
+            } else {
+                Dft<C, false>::run(x[i]);
+#pragma unroll
+                for (int k = 1; k < C; ++k) x[i][k] = cmul(x[i][k], tw[b * k]);
+            }
+#pragma unroll
+            for (int k = 0; k < C; ++k) st_cluster(cluster_addr(mine + off[i], (uint32_t)k), x[i][k]);
+        }
     }
 }
 

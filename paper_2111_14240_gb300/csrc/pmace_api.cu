@@ -48,6 +48,7 @@ struct pmace_job {
     int variant = 0;
     AgentPlanInfo plan{};
     int tiles_x = 0, tiles_y = 0, ntiles = 0;
+    int tile_h = 16;          // gather tile height (rows), width kGatherTileW
 
     float2 *q = nullptr, *u = nullptr, *xbar = nullptr, *probe = nullptr, *dinv = nullptr,
            *tw = nullptr, *img_tmp = nullptr;
@@ -189,7 +190,7 @@ pmace_status build_tables(pmace_job* h, const std::vector<float>& probe_h,
         tw[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
     // scan-overlap lists: for every gather tile the ascending list of windows that intersect it
-    const int TH = kGatherTileH, TW = kGatherTileW;
+    const int TH = h->tile_h, TW = kGatherTileW;
     h->tiles_y = (h->dims.n1 + TH - 1) / TH;
     h->tiles_x = (h->dims.n2 + TW - 1) / TW;
     h->ntiles = h->tiles_x * h->tiles_y;
@@ -384,6 +385,11 @@ pmace_status pmace_create(const pmace_dims* dims, const float* probe, const int3
         h->variant = chosen;
         h->cluster = agent_variant_of(np, chosen).cluster;
     }
+    // gather tile height: PMACE_GATHER_TILE_H in {8, 16, 32}, default 16
+    if (const char* env = std::getenv("PMACE_GATHER_TILE_H")) {
+        const int th = std::atoi(env);
+        if (th == 8 || th == 16 || th == 32) h->tile_h = th;
+    }
 
     // host copies of the small inputs
     std::vector<float> probe_h(2 * P);
@@ -445,7 +451,7 @@ pmace_status pmace_create(const pmace_dims* dims, const float* probe, const int3
     // weight image Lambda^-1
     GatherArgs g = gather_args(h);
     g.lam_out = h->laminv;
-    PM_CREATE(launch_gather_weights(g, h->ntiles, s));
+    PM_CREATE(launch_gather_weights(g, h->ntiles, h->tile_h, s));
 
     // initial stacks
     double sumsq = 0.0;
@@ -515,7 +521,7 @@ pmace_status pmace_iterate(pmace_handle h, int32_t n, const pmace_step* step, vo
             PM_CUDA(h, record_pair(h->ev_agent, h->n_agent, false, s));
             PM_CUDA(h, record_pair(h->ev_cons, h->n_cons, true, s));
         }
-        PM_CUDA(h, launch_gather_consensus(g, h->ntiles, s));
+        PM_CUDA(h, launch_gather_consensus(g, h->ntiles, h->tile_h, s));
         if (h->profiling) PM_CUDA(h, record_pair(h->ev_cons, h->n_cons, false, s));
         h->rho_pending = rho;
         h->iterations++;
@@ -538,7 +544,7 @@ pmace_status pmace_get_image(pmace_handle h, float* out, int out_on_device, void
     g.xbar_in = h->xbar;
     g.out = dst;
     g.two_rho = 2.0f * h->rho_pending;
-    PM_CUDA(h, launch_gather_readout(g, h->ntiles, s));
+    PM_CUDA(h, launch_gather_readout(g, h->ntiles, h->tile_h, s));
     if (!out_on_device) {
         PM_CUDA(h, cudaMemcpyAsync(out, dst, NI * sizeof(float2), cudaMemcpyDeviceToHost, s));
         PM_CUDA(h, cudaStreamSynchronize(s));
@@ -647,7 +653,7 @@ pmace_status pmace_get_plan(pmace_handle h, pmace_plan* plan) {
     plan->cluster = h->cluster;
     plan->threads = h->plan.threads;
     plan->smem_bytes = h->plan.smem_bytes;
-    plan->tile_h = kGatherTileH;
+    plan->tile_h = h->tile_h;
     plan->tile_w = kGatherTileW;
     plan->variant = h->variant;
     plan->cols_per_thread = v.cols_per_thread;

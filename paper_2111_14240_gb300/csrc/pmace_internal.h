@@ -55,22 +55,28 @@ struct GatherArgs {
     float two_rho;          // readout: 2 rho
 };
 
-constexpr int kGatherTileH = 32;
+// Gather tiles are kGatherTileW = 32 pixels wide (one warp per tile row
+// segment) and tile_h rows high, tile_h in {8, 16, 32}; every thread owns
+// kGatherRowsPerThread rows of its column, so a tile has tile_h * 8 threads.
 constexpr int kGatherTileW = 32;
-constexpr int kGatherThreads = 256;
+constexpr int kGatherRowsPerThread = 4;
+__host__ __device__ constexpr int gather_threads(int tile_h) {
+    return tile_h / kGatherRowsPerThread * kGatherTileW;
+}
 
-// Agent kernel variants compiled for each probe size: CTAs per patch,
-// columns per thread in the column step, amplitude staging in shared memory.
+// Agent kernel variants compiled for each probe size: CTAs per window,
+// columns per thread in the column step, amplitude staging in shared memory,
+// windows per cluster.
 // Index 0 is the default; pmace_autotune and PMACE_AGENT_PLAN pick others.
 struct AgentVariant {
-    int cluster, cols_per_thread, stage_y;
+    int cluster, cols_per_thread, stage_y, windows;
 };
 constexpr int kAgentVariants = 4;
 __host__ __device__ constexpr AgentVariant agent_variant_of(int np, int v) {
-    constexpr AgentVariant t32[kAgentVariants] = {{2, 1, 1}, {1, 1, 1}, {2, 1, 0}, {1, 1, 0}};
-    constexpr AgentVariant t64[kAgentVariants] = {{4, 1, 1}, {4, 2, 0}, {2, 1, 1}, {4, 1, 0}};
-    constexpr AgentVariant t128[kAgentVariants] = {{8, 1, 1}, {8, 2, 0}, {4, 1, 1}, {8, 1, 0}};
-    constexpr AgentVariant t256[kAgentVariants] = {{16, 2, 0}, {16, 1, 1}, {8, 1, 1}, {8, 2, 0}};
+    constexpr AgentVariant t32[kAgentVariants] = {{2, 1, 1, 1}, {1, 1, 1, 1}, {2, 1, 0, 2}, {1, 1, 0, 1}};
+    constexpr AgentVariant t64[kAgentVariants] = {{4, 1, 1, 1}, {4, 2, 0, 1}, {2, 1, 1, 1}, {4, 1, 0, 2}};
+    constexpr AgentVariant t128[kAgentVariants] = {{8, 1, 1, 1}, {8, 2, 0, 1}, {4, 1, 1, 1}, {8, 2, 0, 2}};
+    constexpr AgentVariant t256[kAgentVariants] = {{16, 2, 0, 1}, {16, 2, 0, 2}, {8, 1, 1, 1}, {8, 2, 0, 1}};
     return np == 32 ? t32[v] : np == 64 ? t64[v] : np == 128 ? t128[v] : t256[v];
 }
 
@@ -92,9 +98,9 @@ cudaError_t agent_entry_128(const AgentArgs* a, int v, int amp_f16, cudaStream_t
 cudaError_t agent_entry_256(const AgentArgs* a, int v, int amp_f16, cudaStream_t s, AgentPlanInfo* info);
 
 // Support kernels (support.cu).
-cudaError_t launch_gather_weights(const GatherArgs& g, int ntiles, cudaStream_t s);
-cudaError_t launch_gather_consensus(const GatherArgs& g, int ntiles, cudaStream_t s);
-cudaError_t launch_gather_readout(const GatherArgs& g, int ntiles, cudaStream_t s);
+cudaError_t launch_gather_weights(const GatherArgs& g, int ntiles, int tile_h, cudaStream_t s);
+cudaError_t launch_gather_consensus(const GatherArgs& g, int ntiles, int tile_h, cudaStream_t s);
+cudaError_t launch_gather_readout(const GatherArgs& g, int ntiles, int tile_h, cudaStream_t s);
 cudaError_t launch_prep_amps(const void* amps_in, int amp_f16, const float* scales, void* y_out,
                              const int* rowperm, const int* colperm, int J, int np,
                              double* sumsq_partials, int* err_flag, int nblocks, cudaStream_t s);

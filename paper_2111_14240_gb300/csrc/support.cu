@@ -10,7 +10,7 @@ namespace pmace {
 
 // ---------------------------------------------------------------------------
 // Pixel-owner gather over the scan-overlap lists.  One CTA owns a
-// kGatherTileH x kGatherTileW block of image pixels and walks the ascending
+// TH x kGatherTileW block of image pixels and walks the ascending
 // list of windows that intersect it; every pixel sums
 // |d(p - o_i)|^kappa * src_i(p - o_i) over the windows i that contain it in
 // ascending i, so the result is deterministic and needs no atomics.
@@ -18,10 +18,11 @@ namespace pmace {
 //   MODE 1: xbar = Lambda^-1 sum_i P_i^t |D|^kappa u_i                 (G, S6)
 //   MODE 2: x_hat = Lambda^-1 sum_i P_i^t |D|^kappa q_i + 2 rho xbar   (readout)
 // ---------------------------------------------------------------------------
-template <int MODE>
-__global__ void __launch_bounds__(kGatherThreads) gather_kernel(const GatherArgs g) {
-    constexpr int TH = kGatherTileH, TW = kGatherTileW;
-    constexpr int RPT = TH / (kGatherThreads / TW);   // rows per thread
+template <int MODE, int TH>
+__global__ void __launch_bounds__(gather_threads(TH)) gather_kernel(const GatherArgs g) {
+    constexpr int TW = kGatherTileW;
+    constexpr int NT = gather_threads(TH);
+    constexpr int RPT = kGatherRowsPerThread;       // rows per thread
     const int tile = blockIdx.x;
     const int ty0 = (tile / g.tiles_x) * TH, tx0 = (tile % g.tiles_x) * TW;
     const int lane = threadIdx.x % TW, grp = threadIdx.x / TW;
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(const GatherArgs
             const bool inx = have && (unsigned)lx < (unsigned)np;
 #pragma unroll
             for (int r = 0; r < RPT; ++r) {
-                const int py = ty0 + grp + r * (kGatherThreads / TW);
+                const int py = ty0 + grp + r * (NT / TW);
                 const int ly = py - o.x;
                 wgt[k][r] = 0.f;
                 val[k][r] = make_float2(0.f, 0.f);
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(const GatherArgs
     if (px >= g.n2) return;
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
-        const int py = ty0 + grp + r * (kGatherThreads / TW);
+        const int py = ty0 + grp + r * (NT / TW);
         if (py >= g.n1) continue;
         const size_t p = (size_t)py * g.n2 + px;
         if constexpr (MODE == 0) {
@@ -100,14 +101,19 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(const GatherArgs
 }
 
 template <int MODE>
-static cudaError_t launch_gather(const GatherArgs& g, int ntiles, cudaStream_t s) {
+static cudaError_t launch_gather(const GatherArgs& g, int ntiles, int tile_h, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    gather_kernel<MODE><<<ntiles, kGatherThreads, 0, s>>>(g);
+    switch (tile_h) {
+        case 8: gather_kernel<MODE, 8><<<ntiles, gather_threads(8), 0, s>>>(g); break;
+        case 16: gather_kernel<MODE, 16><<<ntiles, gather_threads(16), 0, s>>>(g); break;
+        case 32: gather_kernel<MODE, 32><<<ntiles, gather_threads(32), 0, s>>>(g); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
-cudaError_t launch_gather_weights(const GatherArgs& g, int n, cudaStream_t s) { return launch_gather<0>(g, n, s); }
-cudaError_t launch_gather_consensus(const GatherArgs& g, int n, cudaStream_t s) { return launch_gather<1>(g, n, s); }
-cudaError_t launch_gather_readout(const GatherArgs& g, int n, cudaStream_t s) { return launch_gather<2>(g, n, s); }
+cudaError_t launch_gather_weights(const GatherArgs& g, int n, int th, cudaStream_t s) { return launch_gather<0>(g, n, th, s); }
+cudaError_t launch_gather_consensus(const GatherArgs& g, int n, int th, cudaStream_t s) { return launch_gather<1>(g, n, th, s); }
+cudaError_t launch_gather_readout(const GatherArgs& g, int n, int th, cudaStream_t s) { return launch_gather<2>(g, n, th, s); }
 
 // ---------------------------------------------------------------------------
 // Amplitudes to kernel order: y_k[j][r][c] = y[j][colperm[r]][rowperm[c]]
