@@ -149,6 +149,30 @@ typedef struct {
 } pmace_plan;
 pmace_status pmace_get_plan(pmace_handle h, pmace_plan* plan);
 
+/* Total measured energy sum_j sum_pixels y^2 (FP64, fixed summation order)
+ * of J patterns of np x np amplitudes, without allocating device memory.
+ * The paper has no counterpart: it is the sum pmace_create uses for the
+ * energy-matched start, offered to callers that cannot allocate device
+ * memory (a caller whose device memory is owned by another allocator, or
+ * that must avoid the device-wide synchronisation cudaMalloc/cudaFree can
+ * cause).
+ *   amps   : device pointer, layout of `fmt` (FP32, or FP16 codes with
+ *            device `scales`, y = code * scales[j]).
+ *   out    : device pointer to one double, written asynchronously on `stream`.
+ * Limit: J <= 65536.  Larger J returns PMACE_ERR_INVALID_ARG with a message
+ * from pmace_last_error(NULL); nothing is launched then.
+ * Scratch: the per-window partial sums live in one fixed 512 KB array in the
+ * library's device image, held by every GPU that loads the library until the
+ * process exits and shared by every call.  Each call overwrites the partials
+ * it uses, so nothing needs clearing, but calls whose work overlaps on the
+ * GPU (different streams, or other host threads) race on that array.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  No
+ * device memory is allocated or freed. */
+pmace_status pmace_amplitude_energy_noalloc(const void* amps, pmace_amp_format fmt,
+                                            const float* scales, int32_t J, int32_t np,
+                                            double* out, void* stream);
+
 /* Device bytes held by the job. */
 int64_t pmace_device_bytes(pmace_handle h);
 

@@ -298,6 +298,12 @@ cudaError_t record_pair(std::vector<EventPair>& pool, size_t& n, bool start, cud
 
 }  // namespace
 
+namespace pmace {
+// Record the message pmace_last_error(NULL) returns, for entry points that
+// have no handle.
+void set_unbound_error(const char* msg) { g_create_error = msg ? msg : ""; }
+}  // namespace pmace
+
 extern "C" {
 
 int32_t pmace_abi_version(void) { return 1; }

@@ -113,4 +113,7 @@ cudaError_t launch_patches_from_state(const float2* q, const float2* xbar, const
                                       cudaStream_t s);
 cudaError_t launch_check_finite(const float* data, int64_t n, int* err_flag, cudaStream_t s);
 
+// Message returned by pmace_last_error(NULL) (pmace_api.cu).
+void set_unbound_error(const char* msg);
+
 }  // namespace pmace

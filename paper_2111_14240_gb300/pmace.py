@@ -52,7 +52,8 @@ class pmace_plan(ctypes.Structure):
 EXPORTS = ["pmace_create", "pmace_iterate", "pmace_get_image", "pmace_get_patches",
            "pmace_residual", "pmace_get_state", "pmace_set_state", "pmace_set_profiling",
            "pmace_kernel_times", "pmace_get_plan", "pmace_device_bytes", "pmace_destroy",
-           "pmace_last_error", "pmace_status_string", "pmace_abi_version"]
+           "pmace_last_error", "pmace_status_string", "pmace_abi_version",
+           "pmace_amplitude_energy_noalloc"]
 
 
 def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
@@ -80,6 +81,7 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         "pmace_last_error": (ctypes.c_char_p, [vp]),
         "pmace_status_string": (ctypes.c_char_p, [i32]),
         "pmace_abi_version": (i32, []),
+        "pmace_amplitude_energy_noalloc": (i32, [vp, i32, vp, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -205,6 +207,14 @@ def pmace_get_plan(h):
     p = pmace_plan()
     _check(_lib.pmace_get_plan(h, ctypes.byref(p)), h)
     return {k: getattr(p, k) for k, _ in pmace_plan._fields_}
+
+
+def pmace_amplitude_energy_noalloc(amps, J, np_, out, amp_format=PMACE_AMP_F32, scales=None,
+                                   stream=None):
+    """Sum of y^2 over J np x np patterns into the device double `out`,
+    allocating nothing (see include/pmace.h)."""
+    _check(_lib.pmace_amplitude_energy_noalloc(_ptr(amps), int(amp_format), _ptr(scales), int(J),
+                                               int(np_), _ptr(out), _stream(stream)), None)
 
 
 def pmace_device_bytes(h) -> int:
