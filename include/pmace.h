@@ -94,7 +94,11 @@ pmace_status pmace_create(const pmace_dims* dims, const float* probe, const int3
 
 /* Run n >= 0 iterations of Algorithm 1 (w <- F(v); z <- G(2w - v);
  * v <- v + 2 rho (z - w)) with the given alpha, rho.  Asynchronous; two
- * kernel launches per iteration. */
+ * kernel launches per iteration.  Runs of iterations with an unchanged rho
+ * are replayed from a CUDA graph captured once per (alpha, rho) on a stream
+ * the job owns (set PMACE_GRAPHS=0 in the environment before creating the
+ * job to launch every kernel directly; per-kernel profiling also launches
+ * directly). */
 pmace_status pmace_iterate(pmace_handle h, int32_t n, const pmace_step* step, void* stream);
 
 /* Algorithm 1's output x_hat = Lambda^-1 sum_j P_j^t |D|^kappa v_j for the
@@ -172,6 +176,24 @@ pmace_status pmace_get_plan(pmace_handle h, pmace_plan* plan);
 pmace_status pmace_amplitude_energy_noalloc(const void* amps, pmace_amp_format fmt,
                                             const float* scales, int32_t J, int32_t np,
                                             double* out, void* stream);
+
+/* Select the kernel plan: agent variant `variant` (an index into the
+ * per-probe-size variant table, see pmace_plan) and consensus tile height
+ * tile_h in {8, 16, 32}.  Switching to a variant with another cluster size
+ * re-lays out the stored amplitudes on the device.  Synchronises `stream`.
+ * INVALID_ARG for out-of-range values, UNSUPPORTED_SIZE if the device
+ * cannot run the variant. */
+pmace_status pmace_set_plan(pmace_handle h, int32_t variant, int32_t tile_h, void* stream);
+
+/* Time every runnable agent variant, then every consensus tile height, on
+ * this job's own data (iters timed iterations each, after two untimed ones,
+ * with `step`), keep the fastest plan and report it in *chosen (may be
+ * NULL).  The job's state (stacks, consensus image, iteration count, pending
+ * rho) is saved first and restored afterwards, so tuning does not advance
+ * the reconstruction.  Allocates a temporary copy of the state; synchronises
+ * `stream`. */
+pmace_status pmace_autotune(pmace_handle h, const pmace_step* step, int32_t iters, void* stream,
+                            pmace_plan* chosen);
 
 /* Device bytes held by the job. */
 int64_t pmace_device_bytes(pmace_handle h);

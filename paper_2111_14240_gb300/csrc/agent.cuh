@@ -136,7 +136,8 @@ agent_kernel(const AgentArgs a) {
     constexpr int r1 = G::kRow.first, r2 = G::kRow.second;
     constexpr int S1 = N / r1;
     constexpr int HALF = N / 2;
-    constexpr int BATCH = 4;
+    constexpr int BATCH = 4;                       // element pairs in flight per thread, copy-in
+    constexpr int BATCH_OUT = 4;                   // and copy-out
     constexpr int ROWS = PPC * R;                  // tile rows: PPC windows of R rows
     static_assert(r2 > 1, "row transform needs two stages");
     static_assert(R == 16 || R == 32, "column DFT length must be 16 or 32");
@@ -377,11 +378,11 @@ agent_kernel(const AgentArgs a) {
                 float2* __restrict__ uo = a.u + pbase_of(p);
                 const float2* __restrict__ xb = a.xbar + (size_t)(off.x + rank * R) * a.n2 + off.y;
                 const float2* tp = tile + p * R * RS;
-                for_pairs<N, R, T, BATCH>([&](int i0) {
-                    float4 qv[BATCH], dv[BATCH];
-                    float2 x0[BATCH], x1[BATCH];
+                for_pairs<N, R, T, BATCH_OUT>([&](int i0) {
+                    float4 qv[BATCH_OUT], dv[BATCH_OUT];
+                    float2 x0[BATCH_OUT], x1[BATCH_OUT];
 #pragma unroll
-                    for (int i = 0; i < BATCH; ++i) {
+                    for (int i = 0; i < BATCH_OUT; ++i) {
                         const int t = threadIdx.x + (i0 + i) * T;
                         const int row = t / HALF, c = 2 * (t % HALF);
                         qv[i] = *reinterpret_cast<const float4*>(qp + row * N + c);
@@ -390,7 +391,7 @@ agent_kernel(const AgentArgs a) {
                         x1[i] = __ldg(xb + (size_t)row * a.n2 + c + 1);
                     }
 #pragma unroll
-                    for (int i = 0; i < BATCH; ++i) {
+                    for (int i = 0; i < BATCH_OUT; ++i) {
                         const int t = threadIdx.x + (i0 + i) * T;
                         const int row = t / HALF, c = 2 * (t % HALF);
                         const float2* src = tp + row * RS + pcol(c);

@@ -31,6 +31,7 @@ namespace {
 
 constexpr int kMaxCluster = 16;
 constexpr int kPrepBlocks = 608;
+constexpr int kGraphIters = 8;   // iterations per replay of the captured graph
 
 thread_local std::string g_create_error;
 
@@ -61,6 +62,14 @@ struct pmace_job {
 
     int64_t iterations = 0;
     float rho_pending = 0.5f;
+
+    std::vector<int32_t> offs_host;   // window corners, for rebuilding the overlap lists
+
+    // CUDA graph of kGraphIters steady-state iterations for one (alpha, rho)
+    bool use_graphs = true;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    float graph_alpha = -1.f, graph_rho = -1.f;
 
     bool profiling = false;
     std::vector<EventPair> ev_agent, ev_cons;
@@ -162,6 +171,41 @@ std::vector<int> radices_of(int L) {
     return v;
 }
 
+// For every h->tile_h x kGatherTileW image tile, the ascending list of the
+// windows that intersect it (CSR: cnt[t]..cnt[t+1] index list); sets the
+// tile counts of h.
+void overlap_lists(pmace_job* h, const std::vector<int32_t>& offs_h, std::vector<int>& cnt,
+                   std::vector<int>& list) {
+    const int np = h->dims.np, J = h->dims.J;
+    const int TH = h->tile_h, TW = kGatherTileW;
+    h->tiles_y = (h->dims.n1 + TH - 1) / TH;
+    h->tiles_x = (h->dims.n2 + TW - 1) / TW;
+    h->ntiles = h->tiles_x * h->tiles_y;
+    cnt.assign(h->ntiles + 1, 0);
+    auto tile_range = [&](int j, int& y0, int& y1, int& x0, int& x1) {
+        const int r = offs_h[2 * j], c = offs_h[2 * j + 1];
+        y0 = r / TH;
+        y1 = (r + np - 1) / TH;
+        x0 = c / TW;
+        x1 = (c + np - 1) / TW;
+    };
+    for (int j = 0; j < J; ++j) {
+        int y0, y1, x0, x1;
+        tile_range(j, y0, y1, x0, x1);
+        for (int ty = y0; ty <= y1; ++ty)
+            for (int tx = x0; tx <= x1; ++tx) cnt[ty * h->tiles_x + tx + 1]++;
+    }
+    for (int t = 0; t < h->ntiles; ++t) cnt[t + 1] += cnt[t];
+    list.assign(std::max(cnt[h->ntiles], 1), 0);
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (int j = 0; j < J; ++j) {   // ascending j, so every list is ascending
+        int y0, y1, x0, x1;
+        tile_range(j, y0, y1, x0, x1);
+        for (int ty = y0; ty <= y1; ++ty)
+            for (int tx = x0; tx <= x1; ++tx) list[fill[ty * h->tiles_x + tx]++] = j;
+    }
+}
+
 pmace_status build_tables(pmace_job* h, const std::vector<float>& probe_h,
                           const std::vector<int32_t>& offs_h, cudaStream_t s,
                           std::vector<std::vector<char>>& keep, int** perm_out) {
@@ -190,33 +234,8 @@ pmace_status build_tables(pmace_job* h, const std::vector<float>& probe_h,
         tw[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
     // scan-overlap lists: for every gather tile the ascending list of windows that intersect it
-    const int TH = h->tile_h, TW = kGatherTileW;
-    h->tiles_y = (h->dims.n1 + TH - 1) / TH;
-    h->tiles_x = (h->dims.n2 + TW - 1) / TW;
-    h->ntiles = h->tiles_x * h->tiles_y;
-    std::vector<int> cnt(h->ntiles + 1, 0);
-    auto tile_range = [&](int j, int& y0, int& y1, int& x0, int& x1) {
-        const int r = offs_h[2 * j], c = offs_h[2 * j + 1];
-        y0 = r / TH;
-        y1 = (r + np - 1) / TH;
-        x0 = c / TW;
-        x1 = (c + np - 1) / TW;
-    };
-    for (int j = 0; j < J; ++j) {
-        int y0, y1, x0, x1;
-        tile_range(j, y0, y1, x0, x1);
-        for (int ty = y0; ty <= y1; ++ty)
-            for (int tx = x0; tx <= x1; ++tx) cnt[ty * h->tiles_x + tx + 1]++;
-    }
-    for (int t = 0; t < h->ntiles; ++t) cnt[t + 1] += cnt[t];
-    std::vector<int> list(std::max(cnt[h->ntiles], 1));
-    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
-    for (int j = 0; j < J; ++j) {   // ascending j, so every list is ascending
-        int y0, y1, x0, x1;
-        tile_range(j, y0, y1, x0, x1);
-        for (int ty = y0; ty <= y1; ++ty)
-            for (int tx = x0; tx <= x1; ++tx) list[fill[ty * h->tiles_x + tx]++] = j;
-    }
+    std::vector<int> cnt, list;
+    overlap_lists(h, offs_h, cnt, list);
     // row and column spectrum orders of the agent kernel: the two in-place
     // row stages leave each row digit-reversed; along columns, local row k2
     // of CTA `rank` holds frequency rank + cluster * k2 after the cross-CTA
@@ -276,6 +295,8 @@ void free_job(pmace_job* h) {
             if (e.a) cudaEventDestroy(e.a);
             if (e.b) cudaEventDestroy(e.b);
         }
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     delete h;
 }
 
@@ -303,6 +324,148 @@ namespace pmace {
 // have no handle.
 void set_unbound_error(const char* msg) { g_create_error = msg ? msg : ""; }
 }  // namespace pmace
+
+namespace {
+
+AgentArgs agent_args(const pmace_job* h, float alpha, float rho) {
+    AgentArgs a{};
+    a.q = h->q;
+    a.u = h->u;
+    a.xbar = h->xbar;
+    a.y = h->y;
+    a.yscale = h->yscale;
+    a.probe = h->probe;
+    a.dinv = h->dinv;
+    a.tw = h->tw;
+    a.offs = h->offs;
+    a.partials = h->partials;
+    a.n2 = h->dims.n2;
+    a.J = h->dims.J;
+    a.alpha = alpha;
+    a.rho_cur = rho;
+    a.rho_prev = h->rho_pending;
+    a.first = h->iterations == 0 ? 1 : 0;
+    return a;
+}
+
+// One iteration of Algorithm 1: agent sweep (S0-S5) then consensus (S6).
+pmace_status launch_iteration(pmace_job* h, float alpha, float rho, cudaStream_t s, bool events) {
+    const AgentArgs a = agent_args(h, alpha, rho);
+    GatherArgs g = gather_args(h);
+    g.src = h->u;
+    g.out = h->xbar;
+    if (events) PM_CUDA(h, record_pair(h->ev_agent, h->n_agent, true, s));
+    PM_CUDA(h, agent_entry(h->dims.np, &a, h->variant, h->amp_f16, s, nullptr));
+    if (events) {
+        PM_CUDA(h, record_pair(h->ev_agent, h->n_agent, false, s));
+        PM_CUDA(h, record_pair(h->ev_cons, h->n_cons, true, s));
+    }
+    PM_CUDA(h, launch_gather_consensus(g, h->ntiles, h->tile_h, s));
+    if (events) PM_CUDA(h, record_pair(h->ev_cons, h->n_cons, false, s));
+    h->rho_pending = rho;
+    h->iterations++;
+    return PMACE_OK;
+}
+
+// Capture kGraphIters steady-state iterations (rho_prev = rho, not the
+// first iteration) for (alpha, rho) on the job's own stream, once.
+pmace_status ensure_graph(pmace_job* h, float alpha, float rho) {
+    if (h->graph && h->graph_alpha == alpha && h->graph_rho == rho) return PMACE_OK;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    if (!h->capture_stream) PM_CUDA(h, cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+    const int64_t it_saved = h->iterations;
+    const float rho_saved = h->rho_pending;
+    h->iterations = std::max<int64_t>(it_saved, 1);
+    h->rho_pending = rho;
+    cudaGraph_t graph = nullptr;
+    PM_CUDA(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+    pmace_status st = PMACE_OK;
+    for (int i = 0; i < kGraphIters && st == PMACE_OK; ++i) st = launch_iteration(h, alpha, rho, h->capture_stream, false);
+    cudaError_t e = cudaStreamEndCapture(h->capture_stream, &graph);
+    h->iterations = it_saved;
+    h->rho_pending = rho_saved;
+    if (st != PMACE_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
+    e = cudaGraphInstantiate(&h->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return cuda_fail(h, e, "graph instantiate");
+    }
+    h->graph_alpha = alpha;
+    h->graph_rho = rho;
+    return PMACE_OK;
+}
+
+// Switch the agent variant and the gather tile height.  A different cluster
+// size changes the row order the amplitudes are stored in, so they are
+// re-laid out on the device (through u, which is dead between iterations).
+pmace_status switch_plan(pmace_job* h, int variant, int tile_h, cudaStream_t s) {
+    const int np = h->dims.np, J = h->dims.J;
+    if (variant < 0 || variant >= kAgentVariants)
+        return fail(h, PMACE_ERR_INVALID_ARG, "variant %d not in [0, %d)", variant, kAgentVariants);
+    if (tile_h != 8 && tile_h != 16 && tile_h != 32)
+        return fail(h, PMACE_ERR_INVALID_ARG, "tile_h %d not in {8, 16, 32}", tile_h);
+    if (variant != h->variant) {
+        AgentPlanInfo info{};
+        if (agent_entry(np, nullptr, variant, h->amp_f16, s, &info) != cudaSuccess || !info.launchable) {
+            cudaGetLastError();
+            return fail(h, PMACE_ERR_UNSUPPORTED_SIZE, "agent variant %d cannot run on this device", variant);
+        }
+        const int c_new = agent_variant_of(np, variant).cluster;
+        if (c_new != h->cluster) {
+            const std::vector<int> o_old = column_order(np, h->cluster), o_new = column_order(np, c_new);
+            std::vector<int> inv(np), map(np);
+            for (int g = 0; g < np; ++g) inv[o_old[g]] = g;
+            for (int g = 0; g < np; ++g) map[g] = inv[o_new[g]];   // new row g <- old row map[g]
+            int* map_d = nullptr;
+            PM_CUDA(h, cudaMalloc(&map_d, np * sizeof(int)));
+            const size_t ybytes = (size_t)J * np * np * (h->amp_f16 ? 2 : 4);
+            cudaError_t e = cudaMemcpyAsync(map_d, map.data(), np * sizeof(int), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h->u, h->y, ybytes, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = launch_relayout_rows(h->y, h->u, map_d, J, np, h->amp_f16 ? 2 : 4, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            cudaFree(map_d);
+            if (e != cudaSuccess) return cuda_fail(h, e, "amplitude re-layout");
+        }
+        h->variant = variant;
+        h->cluster = c_new;
+        h->plan = info;
+    }
+    if (tile_h != h->tile_h) {
+        h->tile_h = tile_h;
+        std::vector<int> cnt, list;
+        overlap_lists(h, h->offs_host, cnt, list);
+        int *tp = nullptr, *tl = nullptr;
+        cudaError_t e = cudaMalloc(&tp, cnt.size() * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&tl, list.size() * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemcpy(tp, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(tl, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (tp) cudaFree(tp);
+            if (tl) cudaFree(tl);
+            return cuda_fail(h, e, "overlap lists");
+        }
+        cudaStreamSynchronize(s);
+        cudaFree(h->tile_ptr);
+        cudaFree(h->tile_list);
+        h->tile_ptr = tp;
+        h->tile_list = tl;
+    }
+    if (h->graph) {   // the captured launches refer to the old plan
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    return PMACE_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -400,6 +563,8 @@ pmace_status pmace_create(const pmace_dims* dims, const float* probe, const int3
     // host copies of the small inputs
     std::vector<float> probe_h(2 * P);
     std::vector<int32_t> offs_h(offsets, offsets + 2 * (size_t)J);
+    h->offs_host = offs_h;
+    if (const char* env = std::getenv("PMACE_GRAPHS")) h->use_graphs = std::atoi(env) != 0;
     if (inputs_on_device) {
         cudaError_t e = cudaMemcpy(probe_h.data(), probe, 2 * P * sizeof(float), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return bail(cuda_fail(h, e, "probe copy"));
@@ -500,39 +665,122 @@ pmace_status pmace_iterate(pmace_handle h, int32_t n, const pmace_step* step, vo
         return fail(h, PMACE_ERR_INVALID_ARG, "alpha must be finite and >= 0 (got %g)", alpha);
     if (!(rho > 0.f && rho < 1.f)) return fail(h, PMACE_ERR_INVALID_ARG, "rho must be in (0, 1) (got %g)", rho);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    AgentArgs a{};
-    a.q = h->q;
-    a.u = h->u;
-    a.xbar = h->xbar;
-    a.y = h->y;
-    a.yscale = h->yscale;
-    a.probe = h->probe;
-    a.dinv = h->dinv;
-    a.tw = h->tw;
-    a.offs = h->offs;
-    a.partials = h->partials;
-    a.n2 = h->dims.n2;
-    a.J = h->dims.J;
-    a.alpha = alpha;
-    a.rho_cur = rho;
-    GatherArgs g = gather_args(h);
-    g.src = h->u;
-    g.out = h->xbar;
-    for (int32_t it = 0; it < n; ++it) {
-        a.rho_prev = h->rho_pending;
-        a.first = h->iterations == 0 ? 1 : 0;
-        if (h->profiling) PM_CUDA(h, record_pair(h->ev_agent, h->n_agent, true, s));
-        PM_CUDA(h, agent_entry(h->dims.np, &a, h->variant, h->amp_f16, s, nullptr));
-        if (h->profiling) {
-            PM_CUDA(h, record_pair(h->ev_agent, h->n_agent, false, s));
-            PM_CUDA(h, record_pair(h->ev_cons, h->n_cons, true, s));
+    int32_t done = 0;
+    // Iterations that open with the pending rho of an earlier call (or the
+    // job's first iteration) are launched directly; the steady state
+    // (rho_prev == rho) replays a captured graph of kGraphIters iterations.
+    while (done < n && (h->iterations == 0 || h->rho_pending != rho)) {
+        pmace_status st = launch_iteration(h, alpha, rho, s, h->profiling);
+        if (st != PMACE_OK) return st;
+        ++done;
+    }
+    if (!h->profiling && h->use_graphs && n - done >= kGraphIters) {
+        pmace_status st = ensure_graph(h, alpha, rho);
+        if (st != PMACE_OK) return st;
+        for (; done + kGraphIters <= n; done += kGraphIters) {
+            PM_CUDA(h, cudaGraphLaunch(h->graph, s));
+            h->iterations += kGraphIters;
         }
-        PM_CUDA(h, launch_gather_consensus(g, h->ntiles, h->tile_h, s));
-        if (h->profiling) PM_CUDA(h, record_pair(h->ev_cons, h->n_cons, false, s));
-        h->rho_pending = rho;
-        h->iterations++;
+    }
+    for (; done < n; ++done) {
+        pmace_status st = launch_iteration(h, alpha, rho, s, h->profiling);
+        if (st != PMACE_OK) return st;
     }
     return PMACE_OK;
+}
+
+pmace_status pmace_set_plan(pmace_handle h, int32_t variant, int32_t tile_h, void* stream) {
+    if (!h) return fail(nullptr, PMACE_ERR_INVALID_ARG, "NULL handle");
+    return switch_plan(h, variant, tile_h, static_cast<cudaStream_t>(stream));
+}
+
+pmace_status pmace_autotune(pmace_handle h, const pmace_step* step, int32_t iters, void* stream,
+                            pmace_plan* chosen) {
+    if (!h) return fail(nullptr, PMACE_ERR_INVALID_ARG, "NULL handle");
+    if (!step || iters < 1) return fail(h, PMACE_ERR_INVALID_ARG, "step must be non-NULL and iters >= 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t JP = (size_t)h->dims.J * h->dims.np * h->dims.np, NI = (size_t)h->dims.n1 * h->dims.n2;
+    // save the state; every trial starts from it and it is restored at the end
+    float2 *q0 = nullptr, *x0 = nullptr;
+    cudaError_t e = cudaMalloc(&q0, JP * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&x0, NI * sizeof(float2));
+    if (e != cudaSuccess) {
+        if (q0) cudaFree(q0);
+        return cuda_fail(h, e, "autotune state copy");
+    }
+    const int64_t it0 = h->iterations;
+    const float rho0 = h->rho_pending;
+    const bool prof0 = h->profiling, graphs0 = h->use_graphs;
+    pmace_status st = PMACE_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto restore = [&]() -> cudaError_t {
+        cudaError_t r = cudaMemcpyAsync(h->q, q0, JP * sizeof(float2), cudaMemcpyDeviceToDevice, s);
+        if (r == cudaSuccess) r = cudaMemcpyAsync(h->xbar, x0, NI * sizeof(float2), cudaMemcpyDeviceToDevice, s);
+        h->iterations = it0;
+        h->rho_pending = rho0;
+        return r;
+    };
+    // time `iters` iterations (after two untimed ones) of the current plan, ms per iteration
+    auto trial = [&](double* ms) -> pmace_status {
+        pmace_status r = pmace_iterate(h, 2, step, s);
+        if (r != PMACE_OK) return r;
+        PM_CUDA(h, cudaEventRecord(e0, s));
+        r = pmace_iterate(h, iters, step, s);
+        if (r != PMACE_OK) return r;
+        PM_CUDA(h, cudaEventRecord(e1, s));
+        PM_CUDA(h, cudaEventSynchronize(e1));
+        float t = 0.f;
+        PM_CUDA(h, cudaEventElapsedTime(&t, e0, e1));
+        *ms = t / iters;
+        PM_CUDA(h, restore());
+        return PMACE_OK;
+    };
+    int best_v = h->variant, best_th = h->tile_h;
+    double best = 1e300;
+    h->profiling = false;
+    h->use_graphs = true;
+    e = cudaMemcpyAsync(q0, h->q, JP * sizeof(float2), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(x0, h->xbar, NI * sizeof(float2), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) st = cuda_fail(h, e, "autotune setup");
+    // agent variants at the current tile height, then tile heights for the best variant
+    for (int v = 0; v < kAgentVariants && st == PMACE_OK; ++v) {
+        AgentPlanInfo info{};
+        if (agent_entry(h->dims.np, nullptr, v, h->amp_f16, s, &info) != cudaSuccess || !info.launchable) {
+            cudaGetLastError();
+            continue;
+        }
+        st = switch_plan(h, v, h->tile_h, s);
+        double ms = 0.0;
+        if (st == PMACE_OK) st = trial(&ms);
+        if (st == PMACE_OK && ms < best) {
+            best = ms;
+            best_v = v;
+        }
+    }
+    if (st == PMACE_OK) st = switch_plan(h, best_v, h->tile_h, s);
+    for (int th : {8, 16, 32}) {
+        if (st != PMACE_OK) break;
+        st = switch_plan(h, best_v, th, s);
+        double ms = 0.0;
+        if (st == PMACE_OK) st = trial(&ms);
+        if (st == PMACE_OK && ms < best) {
+            best = ms;
+            best_th = th;
+        }
+    }
+    if (st == PMACE_OK) st = switch_plan(h, best_v, best_th, s);
+    if (restore() != cudaSuccess && st == PMACE_OK) st = fail(h, PMACE_ERR_CUDA, "autotune restore failed");
+    cudaStreamSynchronize(s);
+    h->profiling = prof0;
+    h->use_graphs = graphs0;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(q0);
+    cudaFree(x0);
+    if (st == PMACE_OK && chosen) st = pmace_get_plan(h, chosen);
+    return st;
 }
 
 pmace_status pmace_get_image(pmace_handle h, float* out, int out_on_device, void* stream) {

@@ -112,6 +112,8 @@ cudaError_t launch_patches_from_state(const float2* q, const float2* xbar, const
                                       float2* v, int J, int np, int n2, float two_rho,
                                       cudaStream_t s);
 cudaError_t launch_check_finite(const float* data, int64_t n, int* err_flag, cudaStream_t s);
+cudaError_t launch_relayout_rows(void* dst, const void* src, const int* rowmap, int J, int np, int elem,
+                                 cudaStream_t s);
 
 // Message returned by pmace_last_error(NULL) (pmace_api.cu).
 void set_unbound_error(const char* msg);

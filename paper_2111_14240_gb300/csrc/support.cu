@@ -256,6 +256,27 @@ cudaError_t launch_patches_from_state(const float2* q, const float2* xbar, const
     return cudaGetLastError();
 }
 
+// Row permutation of a [J][np][np] stack of elem-byte values:
+// dst[j][g][c] = src[j][rowmap[g]][c].
+__global__ void relayout_rows_kernel(char* __restrict__ dst, const char* __restrict__ src,
+                                     const int* __restrict__ rowmap, int J, int np, int elem) {
+    const size_t row_bytes = (size_t)np * elem;
+    const size_t total = (size_t)J * np * row_bytes;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t rowi = i / row_bytes, b = i % row_bytes;
+        const size_t j = rowi / np;
+        const int g = (int)(rowi % np);
+        dst[i] = src[(j * np + rowmap[g]) * row_bytes + b];
+    }
+}
+
+cudaError_t launch_relayout_rows(void* dst, const void* src, const int* rowmap, int J, int np, int elem,
+                                 cudaStream_t s) {
+    relayout_rows_kernel<<<1216, 256, 0, s>>>(static_cast<char*>(dst), static_cast<const char*>(src), rowmap,
+                                              J, np, elem);
+    return cudaGetLastError();
+}
+
 __global__ void check_finite_kernel(const float* __restrict__ d, int64_t n, int* __restrict__ err) {
     int bad = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;

@@ -53,7 +53,7 @@ EXPORTS = ["pmace_create", "pmace_iterate", "pmace_get_image", "pmace_get_patche
            "pmace_residual", "pmace_get_state", "pmace_set_state", "pmace_set_profiling",
            "pmace_kernel_times", "pmace_get_plan", "pmace_device_bytes", "pmace_destroy",
            "pmace_last_error", "pmace_status_string", "pmace_abi_version",
-           "pmace_amplitude_energy_noalloc"]
+           "pmace_amplitude_energy_noalloc", "pmace_set_plan", "pmace_autotune"]
 
 
 def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
@@ -82,6 +82,8 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         "pmace_status_string": (ctypes.c_char_p, [i32]),
         "pmace_abi_version": (i32, []),
         "pmace_amplitude_energy_noalloc": (i32, [vp, i32, vp, i32, i32, vp, vp]),
+        "pmace_set_plan": (i32, [vp, i32, i32, vp]),
+        "pmace_autotune": (i32, [vp, P(pmace_step), i32, vp, P(pmace_plan)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -217,6 +219,17 @@ def pmace_amplitude_energy_noalloc(amps, J, np_, out, amp_format=PMACE_AMP_F32, 
                                                int(np_), _ptr(out), _stream(stream)), None)
 
 
+def pmace_set_plan(h, variant, tile_h, stream=None):
+    _check(_lib.pmace_set_plan(h, int(variant), int(tile_h), _stream(stream)), h)
+
+
+def pmace_autotune(h, alpha, rho, iters=10, stream=None):
+    step = pmace_step(float(alpha), float(rho))
+    p = pmace_plan()
+    _check(_lib.pmace_autotune(h, ctypes.byref(step), int(iters), _stream(stream), ctypes.byref(p)), h)
+    return {k: getattr(p, k) for k, _ in pmace_plan._fields_}
+
+
 def pmace_device_bytes(h) -> int:
     return int(_lib.pmace_device_bytes(h))
 
@@ -269,6 +282,12 @@ class Reconstruction:
 
     def plan(self):
         return pmace_get_plan(self.h)
+
+    def set_plan(self, variant, tile_h=16):
+        pmace_set_plan(self.h, variant, tile_h, self.stream)
+
+    def autotune(self, alpha, rho=0.5, iters=10):
+        return pmace_autotune(self.h, alpha, rho, iters, self.stream)
 
     def close(self):
         if self.h:

@@ -1,0 +1,98 @@
+"""Host runtime on the GPU: CUDA-graph replay, plan switching, autotuning."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2111_14240_gb300 import datagen
+from tests.gpu_helpers import TOL_ITER, random_start, rel_l2, rounded_inputs, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2111_14240_gb300 import build
+    build.build()
+
+
+def _job(w, init=None, graphs=True):
+    from paper_2111_14240_gb300 import pmace as pm
+    _, _, probe32, y32 = rounded_inputs(w)
+    old = os.environ.get("PMACE_GRAPHS")
+    os.environ["PMACE_GRAPHS"] = "1" if graphs else "0"
+    try:
+        return pm.Reconstruction(probe32, w.offsets, y32, w.x.shape, init=init)
+    finally:
+        if old is None:
+            os.environ.pop("PMACE_GRAPHS", None)
+        else:
+            os.environ["PMACE_GRAPHS"] = old
+
+
+@pytest.mark.parametrize("cfg", ["small", "p256"])
+def test_graph_replay_is_bit_identical_to_direct_launches(cfg):
+    w = datagen.make_workload(cfg, seed=41)
+    a, b = _job(w, graphs=True), _job(w, graphs=False)
+    for rec in (a, b):
+        rec.iterate(3, 0.5, 0.3)      # changes rho below: direct launches, then graph replays
+        rec.iterate(21, 0.4, 0.5)
+    xa, xb = a.image().cpu().numpy(), b.image().cpu().numpy()
+    va, vb = a.patches().cpu().numpy(), b.patches().cpu().numpy()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert a.residual() == b.residual()
+    a.close()
+    b.close()
+
+
+def test_set_plan_midrun_matches_oracle():
+    """Switching variants (and so the stored amplitude row order) mid-run
+    keeps every later iteration within the parity bound."""
+    w = datagen.make_workload(dict(n_obj=400, n_p=128, probe_sigma=32.0, n_scan=9, step=32,
+                                   jitter=2, peak=1e5, name="mid128"), seed=42)
+    x0 = random_start(w)
+    rec = _job(w, init=x0)
+    rec.iterate(1, 0.5, 0.5)
+    for v, th in [(2, 8), (1, 32), (3, 16), (0, 16)]:
+        rec.set_plan(v, th)
+        assert rec.plan()["variant"] == v and rec.plan()["tile_h"] == th
+        rec.iterate(1, 0.5, 0.5)
+    got = rec.image().cpu().numpy().astype(np.complex128)
+    rec.close()
+    o = run_oracle(w, 5, 0.5, 0.5, x0=x0)
+    assert rel_l2(got, o["x_hat"]) < TOL_ITER
+
+
+def test_autotune_keeps_state_and_picks_a_valid_plan():
+    from paper_2111_14240_gb300 import pmace as pm
+    w = datagen.make_workload("p256", seed=43)
+    x0 = random_start(w)
+    rec = _job(w, init=x0)
+    rec.iterate(4, 0.5, 0.5)
+    before = rec.image().cpu().numpy()
+    r_before = rec.residual()
+    plan = rec.autotune(0.5, 0.5, iters=5)
+    assert 0 <= plan["variant"] < 4 and plan["tile_h"] in (8, 16, 32)
+    after = rec.image().cpu().numpy()
+    assert np.array_equal(before, after)
+    state_iters = pm.pmace_get_state(rec.h, None, None).iterations
+    assert state_iters == 4
+    # continuing with the tuned plan stays within tolerance of a default-plan run
+    rec.iterate(3, 0.5, 0.5)
+    ref = _job(w, init=x0)
+    ref.iterate(7, 0.5, 0.5)
+    assert rel_l2(rec.image().cpu().numpy(), ref.image().cpu().numpy()) < 1e-4
+    assert r_before is not None
+    rec.close()
+    ref.close()
+
+
+def test_set_plan_rejects_bad_values():
+    from paper_2111_14240_gb300 import pmace as pm
+    w = datagen.make_workload("small", seed=44)
+    rec = _job(w)
+    with pytest.raises(pm.PmaceError):
+        rec.set_plan(7, 16)
+    with pytest.raises(pm.PmaceError):
+        rec.set_plan(0, 12)
+    rec.close()
