@@ -195,6 +195,71 @@ pmace_status pmace_set_plan(pmace_handle h, int32_t variant, int32_t tile_h, voi
 pmace_status pmace_autotune(pmace_handle h, const pmace_step* step, int32_t iters, void* stream,
                             pmace_plan* chosen);
 
+/* ---- Serving: continuous batching of reconstruction jobs on one GPU ----
+ * A server owns a worker thread and a CUDA stream on the device current at
+ * creation.  Jobs are queued by pmace_server_submit (from any host thread;
+ * the request's host buffers are copied, so they may be reused on return)
+ * and admitted in arrival order while the device bytes of the admitted jobs
+ * stay within the budget and fewer than max_active_jobs run.  Every tick
+ * runs one iteration (Algorithm 1) for every admitted job, with the
+ * windows of all jobs of one probe size and amplitude format in one agent
+ * launch and the image tiles of all jobs in one consensus launch; a job that
+ * has run its iterations is read out, freed and reported.  A job's result
+ * is the same whether it runs alone or batched with others. */
+typedef struct pmace_server* pmace_server_handle;
+
+typedef struct {
+    int64_t hbm_budget_bytes;  /* 0: 80 % of the device memory free at creation */
+    int32_t max_active_jobs;   /* 0: 64 */
+    int32_t tile_h;            /* consensus tile height for every job: 8, 16 or 32 (0: 16) */
+} pmace_server_config;
+
+/* One job: the arguments of pmace_create (host pointers only, inputs on the
+ * host), the iteration count and the step parameters. */
+typedef struct {
+    pmace_dims dims;
+    const float* probe;
+    const int32_t* offsets;
+    const void* amps;
+    pmace_amp_format fmt;
+    const float* scales;
+    const float* init;
+    pmace_step step;
+    int32_t iterations;
+} pmace_request;
+
+/* Outcome of a job: done = 0 while queued or running.  Times are host
+ * steady-clock milliseconds (submit, admission, completion).  status is the
+ * job's own status (e.g. PMACE_ERR_OOM if it can never fit the budget). */
+typedef struct {
+    int32_t done;
+    int32_t status;
+    double submit_ms, start_ms, finish_ms;
+    int64_t device_bytes;
+} pmace_job_result;
+
+typedef struct {
+    int64_t queued, active, completed, ticks, device_bytes, budget_bytes;
+} pmace_server_counters;
+
+pmace_status pmace_server_create(const pmace_server_config* cfg, pmace_server_handle* out);
+/* Queue a job; *id identifies it in later calls.  INVALID_ARG for a
+ * malformed request (sizes are checked again at admission). */
+pmace_status pmace_server_submit(pmace_server_handle s, const pmace_request* req, int64_t* id);
+/* Non-blocking: fills *res (res->done = 0 if not finished yet) and, for a
+ * finished job, copies its image x_hat (n1*n2 complex, host) to `image`
+ * when non-NULL.  Results stay available until pmace_server_release. */
+pmace_status pmace_server_poll(pmace_server_handle s, int64_t id, pmace_job_result* res, float* image);
+/* As poll, but waits up to timeout_ms for the job; PMACE_ERR_TIMEOUT if it
+ * has not finished by then (the job keeps running). */
+pmace_status pmace_server_wait(pmace_server_handle s, int64_t id, int32_t timeout_ms, pmace_job_result* res,
+                               float* image);
+/* Forget a finished job's result (frees its host image). */
+pmace_status pmace_server_release(pmace_server_handle s, int64_t id);
+pmace_status pmace_server_stats(pmace_server_handle s, pmace_server_counters* stats);
+/* Stop the worker (jobs still queued or running are dropped) and free everything. */
+void pmace_server_destroy(pmace_server_handle s);
+
 /* Device bytes held by the job. */
 int64_t pmace_device_bytes(pmace_handle h);
 

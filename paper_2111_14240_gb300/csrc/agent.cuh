@@ -127,10 +127,9 @@ __device__ __forceinline__ void for_pairs(F&& f) {
     for (int i0 = 0; i0 < PPT; i0 += BATCH) f(i0);
 }
 
-// MINB: resident CTAs per SM the register allocation is sized for.
-template <int N, int C, int CPT, int YST, int PPC, int AMP, int MINB>
-__global__ void __launch_bounds__(AgentGeom<N, C, CPT, YST, PPC, AMP>::kThreads, MINB)
-agent_kernel(const AgentArgs a) {
+// The sweep of one cluster: windows j0 .. j0 + PPC - 1 of the job `a`.
+template <int N, int C, int CPT, int YST, int PPC, int AMP>
+__device__ __forceinline__ void agent_body(const AgentArgs& a, const int j0) {
     using G = AgentGeom<N, C, CPT, YST, PPC, AMP>;
     constexpr int R = G::R, RS = G::RS, T = G::kThreads, NW = G::kWarps;
     constexpr int r1 = G::kRow.first, r2 = G::kRow.second;
@@ -151,7 +150,6 @@ agent_kernel(const AgentArgs a) {
 
     int rank = 0;
     if constexpr (C > 1) rank = (int)cg::this_cluster().block_rank();
-    const int j0 = (blockIdx.x / C) * PPC;         // first window of this cluster
 
     // window p of the cluster: j0 + p; it may lie past the end (J not a
     // multiple of PPC), in which case its rows are computed on zeros and
@@ -416,6 +414,23 @@ agent_kernel(const AgentArgs a) {
     }
 }
 
+// One job: cluster k processes windows k*PPC .. k*PPC + PPC - 1.
+// MINB: resident CTAs per SM the register allocation is sized for.
+template <int N, int C, int CPT, int YST, int PPC, int AMP, int MINB>
+__global__ void __launch_bounds__(AgentGeom<N, C, CPT, YST, PPC, AMP>::kThreads, MINB)
+agent_kernel(const __grid_constant__ AgentArgs a) {
+    agent_body<N, C, CPT, YST, PPC, AMP>(a, (int)(blockIdx.x / C) * PPC);
+}
+
+// Several jobs in one launch: cluster k processes job work[k].x from window
+// work[k].y on, with that job's arguments descs[work[k].x].
+template <int N, int C, int CPT, int YST, int PPC, int AMP, int MINB>
+__global__ void __launch_bounds__(AgentGeom<N, C, CPT, YST, PPC, AMP>::kThreads, MINB)
+agent_kernel_batched(const AgentArgs* __restrict__ descs, const int2* __restrict__ work) {
+    const int2 w = work[blockIdx.x / C];
+    agent_body<N, C, CPT, YST, PPC, AMP>(descs[w.x], w.y);
+}
+
 template <int N, int C, int CPT, int YST, int PPC, int AMP, int MINB>
 cudaError_t launch_agent_impl(const AgentArgs& a, cudaStream_t s) {
     using G = AgentGeom<N, C, CPT, YST, PPC, AMP>;
@@ -439,6 +454,32 @@ cudaError_t launch_agent_impl(const AgentArgs& a, cudaStream_t s) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, fn, a);
+}
+
+template <int N, int C, int CPT, int YST, int PPC, int AMP, int MINB>
+cudaError_t launch_agent_batched_impl(const AgentArgs* descs, const int2* work, int nclusters, cudaStream_t s) {
+    using G = AgentGeom<N, C, CPT, YST, PPC, AMP>;
+    void (*fn)(const AgentArgs*, const int2*) = agent_kernel_batched<N, C, CPT, YST, PPC, AMP, MINB>;
+    if (nclusters <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem);
+    if (e != cudaSuccess) return e;
+    if constexpr (C > 1) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nclusters * C), 1, 1);
+    cfg.blockDim = dim3(G::kThreads, 1, 1);
+    cfg.dynamicSmemBytes = G::kSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, descs, work);
 }
 
 // How many clusters of this plan the device holds at once (0: not launchable).
@@ -481,6 +522,17 @@ int plan_max_clusters_impl() {
         return 0;
     }
     return nclusters;
+}
+
+// One plan, several jobs: `work` holds nclusters (job, first window) pairs.
+template <int N, int C, int CPT, int YST, int PPC>
+cudaError_t agent_variant_batched(const AgentArgs* descs, const int2* work, int nclusters, int amp_f16,
+                                  cudaStream_t s) {
+    if (amp_f16)
+        return launch_agent_batched_impl<N, C, CPT, YST, PPC, 1, AgentGeom<N, C, CPT, YST, PPC, 1>::kMinBlocks>(
+            descs, work, nclusters, s);
+    return launch_agent_batched_impl<N, C, CPT, YST, PPC, 0, AgentGeom<N, C, CPT, YST, PPC, 0>::kMinBlocks>(
+        descs, work, nclusters, s);
 }
 
 // One plan: query (a == nullptr) or launch, for either amplitude format.

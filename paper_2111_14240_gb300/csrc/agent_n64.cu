@@ -27,4 +27,15 @@ cudaError_t agent_entry_64(const AgentArgs* a, int v, int amp_f16, cudaStream_t 
     }
 }
 
+cudaError_t agent_entry_batched_64(const AgentArgs* descs, const int2* work, int nclusters, int v, int amp_f16,
+                                  cudaStream_t s) {
+    switch (v) {
+        case 0: return agent_variant_batched<64, 4, 1, 1, 1>(descs, work, nclusters, amp_f16, s);
+        case 1: return agent_variant_batched<64, 4, 2, 0, 1>(descs, work, nclusters, amp_f16, s);
+        case 2: return agent_variant_batched<64, 2, 1, 1, 1>(descs, work, nclusters, amp_f16, s);
+        case 3: return agent_variant_batched<64, 4, 1, 0, 2>(descs, work, nclusters, amp_f16, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace pmace

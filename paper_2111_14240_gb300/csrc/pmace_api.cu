@@ -10,6 +10,7 @@
 // lists.  One iteration of Algorithm 1 is two launches: the fused agent
 // sweep (agent.cuh) and the pixel-owner consensus gather (support.cu).
 #include "pmace.h"
+#include "job.h"
 #include "pmace_internal.h"
 
 #include <cuda_fp16.h>
@@ -35,48 +36,9 @@ constexpr int kGraphIters = 8;   // iterations per replay of the captured graph
 
 thread_local std::string g_create_error;
 
-struct EventPair {
-    cudaEvent_t a = nullptr, b = nullptr;
-};
 
 }  // namespace
 
-struct pmace_job {
-    int device = 0;
-    pmace_dims dims{};
-    int amp_f16 = 0;
-    int cluster = 1;
-    int variant = 0;
-    AgentPlanInfo plan{};
-    int tiles_x = 0, tiles_y = 0, ntiles = 0;
-    int tile_h = 16;          // gather tile height (rows), width kGatherTileW
-
-    float2 *q = nullptr, *u = nullptr, *xbar = nullptr, *probe = nullptr, *dinv = nullptr,
-           *tw = nullptr, *img_tmp = nullptr;
-    void* y = nullptr;
-    float *yscale = nullptr, *laminv = nullptr, *wk = nullptr;
-    int2* offs = nullptr;
-    int *tile_ptr = nullptr, *tile_list = nullptr, *err = nullptr;
-    double *partials = nullptr, *red_out = nullptr;
-    int64_t bytes = 0;
-
-    int64_t iterations = 0;
-    float rho_pending = 0.5f;
-
-    std::vector<int32_t> offs_host;   // window corners, for rebuilding the overlap lists
-
-    // CUDA graph of kGraphIters steady-state iterations for one (alpha, rho)
-    bool use_graphs = true;
-    cudaStream_t capture_stream = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    float graph_alpha = -1.f, graph_rho = -1.f;
-
-    bool profiling = false;
-    std::vector<EventPair> ev_agent, ev_cons;
-    size_t n_agent = 0, n_cons = 0;
-
-    std::string error;
-};
 
 namespace {
 
@@ -269,19 +231,6 @@ pmace_status build_tables(pmace_job* h, const std::vector<float>& probe_h,
     return PMACE_OK;
 }
 
-GatherArgs gather_args(const pmace_job* h) {
-    GatherArgs g{};
-    g.wk = h->wk;
-    g.offs = h->offs;
-    g.tile_ptr = h->tile_ptr;
-    g.tile_list = h->tile_list;
-    g.laminv = h->laminv;
-    g.n1 = h->dims.n1;
-    g.n2 = h->dims.n2;
-    g.np = h->dims.np;
-    g.tiles_x = h->tiles_x;
-    return g;
-}
 
 void free_job(pmace_job* h) {
     if (!h) return;
@@ -323,9 +272,20 @@ namespace pmace {
 // Record the message pmace_last_error(NULL) returns, for entry points that
 // have no handle.
 void set_unbound_error(const char* msg) { g_create_error = msg ? msg : ""; }
-}  // namespace pmace
 
-namespace {
+GatherArgs gather_args(const pmace_job* h) {
+    GatherArgs g{};
+    g.wk = h->wk;
+    g.offs = h->offs;
+    g.tile_ptr = h->tile_ptr;
+    g.tile_list = h->tile_list;
+    g.laminv = h->laminv;
+    g.n1 = h->dims.n1;
+    g.n2 = h->dims.n2;
+    g.np = h->dims.np;
+    g.tiles_x = h->tiles_x;
+    return g;
+}
 
 AgentArgs agent_args(const pmace_job* h, float alpha, float rho) {
     AgentArgs a{};
@@ -347,6 +307,10 @@ AgentArgs agent_args(const pmace_job* h, float alpha, float rho) {
     a.first = h->iterations == 0 ? 1 : 0;
     return a;
 }
+}  // namespace pmace
+
+namespace {
+
 
 // One iteration of Algorithm 1: agent sweep (S0-S5) then consensus (S6).
 pmace_status launch_iteration(pmace_job* h, float alpha, float rho, cudaStream_t s, bool events) {

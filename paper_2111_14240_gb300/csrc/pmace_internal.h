@@ -75,7 +75,7 @@ constexpr int kAgentVariants = 4;
 __host__ __device__ constexpr AgentVariant agent_variant_of(int np, int v) {
     constexpr AgentVariant t32[kAgentVariants] = {{2, 1, 1, 1}, {1, 1, 1, 1}, {2, 1, 0, 2}, {1, 1, 0, 1}};
     constexpr AgentVariant t64[kAgentVariants] = {{4, 1, 1, 1}, {4, 2, 0, 1}, {2, 1, 1, 1}, {4, 1, 0, 2}};
-    constexpr AgentVariant t128[kAgentVariants] = {{8, 1, 1, 1}, {8, 2, 0, 1}, {4, 1, 1, 1}, {8, 2, 0, 2}};
+    constexpr AgentVariant t128[kAgentVariants] = {{8, 2, 0, 1}, {8, 1, 1, 1}, {4, 1, 1, 1}, {8, 2, 0, 2}};
     constexpr AgentVariant t256[kAgentVariants] = {{16, 2, 0, 1}, {16, 2, 0, 2}, {8, 1, 1, 1}, {8, 2, 0, 1}};
     return np == 32 ? t32[v] : np == 64 ? t64[v] : np == 128 ? t128[v] : t256[v];
 }
@@ -96,11 +96,23 @@ cudaError_t agent_entry_32(const AgentArgs* a, int v, int amp_f16, cudaStream_t 
 cudaError_t agent_entry_64(const AgentArgs* a, int v, int amp_f16, cudaStream_t s, AgentPlanInfo* info);
 cudaError_t agent_entry_128(const AgentArgs* a, int v, int amp_f16, cudaStream_t s, AgentPlanInfo* info);
 cudaError_t agent_entry_256(const AgentArgs* a, int v, int amp_f16, cudaStream_t s, AgentPlanInfo* info);
+// Several jobs of one probe size and amplitude format in one launch:
+// `descs` (device) holds each job's arguments, `work` (device) the
+// (job, first window) pair of each of the nclusters clusters.
+cudaError_t agent_entry_batched_32(const AgentArgs* descs, const int2* work, int nclusters, int v, int amp_f16, cudaStream_t s);
+cudaError_t agent_entry_batched_64(const AgentArgs* descs, const int2* work, int nclusters, int v, int amp_f16, cudaStream_t s);
+cudaError_t agent_entry_batched_128(const AgentArgs* descs, const int2* work, int nclusters, int v, int amp_f16, cudaStream_t s);
+cudaError_t agent_entry_batched_256(const AgentArgs* descs, const int2* work, int nclusters, int v, int amp_f16, cudaStream_t s);
 
 // Support kernels (support.cu).
 cudaError_t launch_gather_weights(const GatherArgs& g, int ntiles, int tile_h, cudaStream_t s);
 cudaError_t launch_gather_consensus(const GatherArgs& g, int ntiles, int tile_h, cudaStream_t s);
 cudaError_t launch_gather_readout(const GatherArgs& g, int ntiles, int tile_h, cudaStream_t s);
+// Consensus of several jobs in one launch: `work` (device) holds the
+// (job, tile) pair of each of the ntiles CTAs, `descs` (device) each job's
+// arguments; every job uses the same tile height.
+cudaError_t launch_gather_consensus_batched(const GatherArgs* descs, const int2* work, int ntiles, int tile_h,
+                                            cudaStream_t s);
 cudaError_t launch_prep_amps(const void* amps_in, int amp_f16, const float* scales, void* y_out,
                              const int* rowperm, const int* colperm, int J, int np,
                              double* sumsq_partials, int* err_flag, int nblocks, cudaStream_t s);

@@ -19,11 +19,10 @@ namespace pmace {
 //   MODE 2: x_hat = Lambda^-1 sum_i P_i^t |D|^kappa q_i + 2 rho xbar   (readout)
 // ---------------------------------------------------------------------------
 template <int MODE, int TH>
-__global__ void __launch_bounds__(gather_threads(TH)) gather_kernel(const GatherArgs g) {
+__device__ __forceinline__ void gather_body(const GatherArgs& g, const int tile) {
     constexpr int TW = kGatherTileW;
     constexpr int NT = gather_threads(TH);
     constexpr int RPT = kGatherRowsPerThread;       // rows per thread
-    const int tile = blockIdx.x;
     const int ty0 = (tile / g.tiles_x) * TH, tx0 = (tile % g.tiles_x) * TW;
     const int lane = threadIdx.x % TW, grp = threadIdx.x / TW;
     const int px = tx0 + lane;
@@ -100,6 +99,19 @@ __global__ void __launch_bounds__(gather_threads(TH)) gather_kernel(const Gather
     }
 }
 
+template <int MODE, int TH>
+__global__ void __launch_bounds__(gather_threads(TH)) gather_kernel(const __grid_constant__ GatherArgs g) {
+    gather_body<MODE, TH>(g, blockIdx.x);
+}
+
+// Several jobs' tiles in one launch: CTA k gathers tile work[k].y of job work[k].x.
+template <int MODE, int TH>
+__global__ void __launch_bounds__(gather_threads(TH))
+gather_kernel_batched(const GatherArgs* __restrict__ descs, const int2* __restrict__ work) {
+    const int2 w = work[blockIdx.x];
+    gather_body<MODE, TH>(descs[w.x], w.y);
+}
+
 template <int MODE>
 static cudaError_t launch_gather(const GatherArgs& g, int ntiles, int tile_h, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
@@ -114,6 +126,18 @@ static cudaError_t launch_gather(const GatherArgs& g, int ntiles, int tile_h, cu
 cudaError_t launch_gather_weights(const GatherArgs& g, int n, int th, cudaStream_t s) { return launch_gather<0>(g, n, th, s); }
 cudaError_t launch_gather_consensus(const GatherArgs& g, int n, int th, cudaStream_t s) { return launch_gather<1>(g, n, th, s); }
 cudaError_t launch_gather_readout(const GatherArgs& g, int n, int th, cudaStream_t s) { return launch_gather<2>(g, n, th, s); }
+
+cudaError_t launch_gather_consensus_batched(const GatherArgs* descs, const int2* work, int ntiles, int tile_h,
+                                            cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    switch (tile_h) {
+        case 8: gather_kernel_batched<1, 8><<<ntiles, gather_threads(8), 0, s>>>(descs, work); break;
+        case 16: gather_kernel_batched<1, 16><<<ntiles, gather_threads(16), 0, s>>>(descs, work); break;
+        case 32: gather_kernel_batched<1, 32><<<ntiles, gather_threads(32), 0, s>>>(descs, work); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------------------
 // Amplitudes to kernel order: y_k[j][r][c] = y[j][colperm[r]][rowperm[c]]

@@ -49,11 +49,35 @@ class pmace_plan(ctypes.Structure):
                 ("max_clusters", ctypes.c_int32)]
 
 
+class pmace_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_active_jobs", ctypes.c_int32),
+                ("tile_h", ctypes.c_int32)]
+
+
+class pmace_request(ctypes.Structure):
+    _fields_ = [("dims", pmace_dims), ("probe", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+                ("amps", ctypes.c_void_p), ("fmt", ctypes.c_int32), ("scales", ctypes.c_void_p),
+                ("init", ctypes.c_void_p), ("step", pmace_step), ("iterations", ctypes.c_int32)]
+
+
+class pmace_job_result(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int32), ("submit_ms", ctypes.c_double),
+                ("start_ms", ctypes.c_double), ("finish_ms", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64)]
+
+
+class pmace_server_counters(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in
+                ("queued", "active", "completed", "ticks", "device_bytes", "budget_bytes")]
+
+
 EXPORTS = ["pmace_create", "pmace_iterate", "pmace_get_image", "pmace_get_patches",
            "pmace_residual", "pmace_get_state", "pmace_set_state", "pmace_set_profiling",
            "pmace_kernel_times", "pmace_get_plan", "pmace_device_bytes", "pmace_destroy",
            "pmace_last_error", "pmace_status_string", "pmace_abi_version",
-           "pmace_amplitude_energy_noalloc", "pmace_set_plan", "pmace_autotune"]
+           "pmace_amplitude_energy_noalloc", "pmace_set_plan", "pmace_autotune",
+           "pmace_server_create", "pmace_server_submit", "pmace_server_poll", "pmace_server_wait",
+           "pmace_server_release", "pmace_server_stats", "pmace_server_destroy"]
 
 
 def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
@@ -84,6 +108,13 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         "pmace_amplitude_energy_noalloc": (i32, [vp, i32, vp, i32, i32, vp, vp]),
         "pmace_set_plan": (i32, [vp, i32, i32, vp]),
         "pmace_autotune": (i32, [vp, P(pmace_step), i32, vp, P(pmace_plan)]),
+        "pmace_server_create": (i32, [P(pmace_server_config), P(vp)]),
+        "pmace_server_submit": (i32, [vp, P(pmace_request), P(i64)]),
+        "pmace_server_poll": (i32, [vp, i64, P(pmace_job_result), vp]),
+        "pmace_server_wait": (i32, [vp, i64, i32, P(pmace_job_result), vp]),
+        "pmace_server_release": (i32, [vp, i64]),
+        "pmace_server_stats": (i32, [vp, P(pmace_server_counters)]),
+        "pmace_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -316,3 +347,72 @@ def _as_pairs(z, dev):
     if z.is_complex():
         z = torch.view_as_real(z.to(torch.complex64).contiguous())
     return z.to(dev).float().contiguous()
+
+
+# ----------------------------------------------------------------- serving
+def _result_dict(r):
+    return {k: getattr(r, k) for k, _ in pmace_job_result._fields_}
+
+
+class Server:
+    """Continuous-batching server (pmace_server_*): jobs are submitted with
+    host arrays and read back as host images."""
+
+    def __init__(self, hbm_budget_bytes=0, max_active_jobs=0, tile_h=0):
+        cfg = pmace_server_config(int(hbm_budget_bytes), int(max_active_jobs), int(tile_h))
+        self.h = ctypes.c_void_p()
+        _check(_lib.pmace_server_create(ctypes.byref(cfg), ctypes.byref(self.h)), None)
+        self.shapes = {}
+
+    def submit(self, probe, offsets, amps, image_shape, iterations, alpha, rho=0.5, kappa=1.25,
+               amp_format=PMACE_AMP_F32, scales=None, init=None):
+        probe = np.ascontiguousarray(np.asarray(probe, dtype=np.complex64)).view(np.float32)
+        offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+        amps = np.ascontiguousarray(amps)
+        n1, n2 = int(image_shape[0]), int(image_shape[1])
+        sc = None if scales is None else np.ascontiguousarray(np.asarray(scales, dtype=np.float32))
+        ini = None if init is None else np.ascontiguousarray(
+            np.asarray(init, dtype=np.complex64)).view(np.float32)
+        req = pmace_request(pmace_dims(n1, n2, int(probe.shape[0]), int(offs.shape[0]), float(kappa)),
+                            _ptr(probe), _ptr(offs), _ptr(amps), int(amp_format), _ptr(sc), _ptr(ini),
+                            pmace_step(float(alpha), float(rho)), int(iterations))
+        jid = ctypes.c_int64()
+        _check(_lib.pmace_server_submit(self.h, ctypes.byref(req), ctypes.byref(jid)), None)
+        self.shapes[jid.value] = (n1, n2)
+        return jid.value
+
+    def _image_buf(self, jid):
+        n1, n2 = self.shapes[jid]
+        return np.empty((n1, n2), dtype=np.complex64)
+
+    def poll(self, jid):
+        res = pmace_job_result()
+        img = self._image_buf(jid)
+        _check(_lib.pmace_server_poll(self.h, jid, ctypes.byref(res), _ptr(img)), None)
+        return _result_dict(res), (img if res.done and res.status == PMACE_OK else None)
+
+    def wait(self, jid, timeout_ms=600000):
+        res = pmace_job_result()
+        img = self._image_buf(jid)
+        _check(_lib.pmace_server_wait(self.h, jid, int(timeout_ms), ctypes.byref(res), _ptr(img)), None)
+        return _result_dict(res), (img if res.status == PMACE_OK else None)
+
+    def release(self, jid):
+        _check(_lib.pmace_server_release(self.h, jid), None)
+        self.shapes.pop(jid, None)
+
+    def stats(self):
+        c = pmace_server_counters()
+        _check(_lib.pmace_server_stats(self.h, ctypes.byref(c)), None)
+        return {k: getattr(c, k) for k, _ in pmace_server_counters._fields_}
+
+    def close(self):
+        if self.h:
+            _lib.pmace_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
