@@ -320,6 +320,110 @@ def run_ours(args):
     return 0
 
 
+# --------------------------------------------------------------------- serving
+def serving_jobs(n_jobs: int, pool_size: int, seed: int = 7):
+    """Seeded job stream for the serving workload: object side in {256, 512,
+    768, 1024}, probe 64 or 128 (sigma Np/4), raster step U{8..24} px with
+    +-2 px jitter, Poisson peak log-uniform in [1e3, 1e6], 50-150
+    iterations, FP16 amplitudes with per-pattern scales.  The measurements
+    of `pool_size` distinct problems are simulated once and shared by the
+    jobs (each job draws its problem, iteration count and alpha)."""
+    from paper_2111_14240_gb300 import datagen
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pool = []
+    for k in range(pool_size):
+        side = int(rng.choice([256, 512, 768, 1024]))
+        n_p = int(rng.choice([64, 128]))
+        step = int(rng.integers(8, 25))
+        n_scan = (side - n_p) // step + 1
+        peak = float(10 ** rng.uniform(3, 6))
+        cfg = dict(n_obj=side, n_p=n_p, probe_sigma=n_p / 4, n_scan=n_scan, step=step, jitter=2,
+                   peak=peak, name=f"serve{k}")
+        w = datagen.make_workload(cfg, seed=1000 + k)
+        codes, scales = datagen.quantize_amplitudes_f16(w.y)
+        pool.append(dict(w=w, probe=w.probe.astype(np.complex64), codes=codes, scales=scales,
+                         y32=w.y.astype(np.float32)))
+    jobs = []
+    for i in range(n_jobs):
+        jobs.append(dict(p=int(rng.integers(0, pool_size)), iters=int(rng.integers(50, 151)),
+                         alpha=float(rng.uniform(0.3, 1.0)), u=float(rng.random())))
+    return pool, jobs
+
+
+def run_serve(args):
+    import torch
+    from paper_2111_14240_gb300 import pmace as pm
+    torch.cuda.set_device(0)
+    pool, jobs = serving_jobs(args.serve_jobs, args.serve_pool)
+    updates = [pool[j["p"]]["w"].J * j["iters"] for j in jobs]
+    # plain FP32 single-job path: each job's service time, one at a time
+    service = []
+    for j in jobs:
+        d = pool[j["p"]]
+        w = d["w"]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = pm.pmace_create(w.x.shape[0], w.x.shape[1], w.np_, w.J, KAPPA,
+                            np.ascontiguousarray(d["probe"]).view(np.float32), w.offsets, d["y32"],
+                            pm.PMACE_AMP_F32, inputs_on_device=False)
+        pm.pmace_iterate(h, j["iters"], j["alpha"], RHO)
+        img = np.empty(w.x.shape, np.complex64)
+        pm.pmace_get_image(h, img)
+        pm.pmace_destroy(h)
+        service.append(time.perf_counter() - t0)
+    total_service = sum(service)
+    rate = args.serve_load * len(jobs) / total_service          # arrivals per second
+    gaps = [-math.log(1.0 - j["u"]) / rate for j in jobs]
+    arrivals = np.cumsum(gaps)
+    # FIFO one-at-a-time latencies for the same arrivals
+    t = 0.0
+    lat_single = []
+    for a, s in zip(arrivals, service):
+        t = max(t, a) + s
+        lat_single.append(t - a)
+    makespan_single = t
+    # serving run in real time
+    srv = pm.Server(fill_pixels=args.serve_fill)
+    ids = []
+    t_start = time.perf_counter()
+    for j, a in zip(jobs, arrivals):
+        delay = t_start + a - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        d = pool[j["p"]]
+        w = d["w"]
+        ids.append(srv.submit(d["probe"], w.offsets, d["codes"], w.x.shape, j["iters"], j["alpha"], RHO,
+                              amp_format=pm.PMACE_AMP_F16_SCALED, scales=d["scales"]))
+    lat = []
+    last = 0.0
+    for jid in ids:
+        res, _ = srv.wait(jid)
+        assert res["status"] == 0, res
+        lat.append((res["finish_ms"] - res["submit_ms"]) / 1e3)
+        last = max(last, res["finish_ms"])
+        srv.release(jid)
+    makespan = time.perf_counter() - t_start
+    srv.close()
+    tot = float(sum(updates))
+    line = {
+        "metric": "PMACE serving job latency p50/p99 + patch-updates/s", "unit": "s",
+        "value": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+        "higher_is_better": False, "n_gpus": 1, "jobs": len(jobs), "data": "synthetic",
+        "throughput": tot / makespan, "throughput_unit": "patch-updates/s",
+        "load": args.serve_load, "arrival_rate_per_s": rate, "fill_pixels": args.serve_fill,
+        "single_job_fp32": {"p50": float(np.percentile(lat_single, 50)),
+                            "p99": float(np.percentile(lat_single, 99)),
+                            "throughput": tot / makespan_single,
+                            "sum_service_s": total_service},
+        "config": {"workload": "serving: seeded job stream, Poisson arrivals at the given fraction of the "
+                               "single-job path's capacity; object side {256,512,768,1024}, probe 64/128, "
+                               "step 8-24 px +-2, peak 1e3-1e6, 50-150 iterations, FP16 amplitudes; "
+                               f"{args.serve_pool} distinct problems shared by {len(jobs)} jobs"},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -328,7 +432,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--serve-jobs", type=int, default=256)
+    ap.add_argument("--serve-pool", type=int, default=16)
+    ap.add_argument("--serve-load", type=float, default=0.8)
+    ap.add_argument("--serve-fill", type=int, default=0, help="server fill target in pixels (0: default)")
     args = ap.parse_args()
+    if args.serve:
+        return run_serve(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

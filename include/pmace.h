@@ -196,11 +196,12 @@ pmace_status pmace_autotune(pmace_handle h, const pmace_step* step, int32_t iter
                             pmace_plan* chosen);
 
 /* ---- Serving: continuous batching of reconstruction jobs on one GPU ----
- * A server owns a worker thread and a CUDA stream on the device current at
- * creation.  Jobs are queued by pmace_server_submit (from any host thread;
+ * A server owns a worker thread (ticks), an admitter thread (job creation
+ * and freeing) and two CUDA streams on the device current at creation.  Jobs are queued by pmace_server_submit (from any host thread;
  * the request's host buffers are copied, so they may be reused on return)
  * and admitted in arrival order while the device bytes of the admitted jobs
- * stay within the budget and fewer than max_active_jobs run.  Every tick
+ * stay within the budget, fewer than max_active_jobs run and the admitted
+ * jobs do not already fill a tick (fill_pixels).  Every tick
  * runs one iteration (Algorithm 1) for every admitted job, with the
  * windows of all jobs of one probe size and amplitude format in one agent
  * launch and the image tiles of all jobs in one consensus launch; a job that
@@ -212,6 +213,8 @@ typedef struct {
     int64_t hbm_budget_bytes;  /* 0: 80 % of the device memory free at creation */
     int32_t max_active_jobs;   /* 0: 64 */
     int32_t tile_h;            /* consensus tile height for every job: 8, 16 or 32 (0: 16) */
+    int64_t fill_pixels;       /* admit while the admitted jobs' window pixels per tick
+                                  (sum of J * Np^2) stay below this; 0: 2^27 */
 } pmace_server_config;
 
 /* One job: the arguments of pmace_create (host pointers only, inputs on the

@@ -1,9 +1,11 @@
 // Serving loop: continuous batching of PMACE reconstruction jobs on one GPU.
 //
 // Jobs (each a full problem: image size, probe, scan, amplitudes, iteration
-// count, alpha, rho) are submitted from any host thread and queued.  A
-// worker thread admits queued jobs in arrival order while the device bytes
-// of the admitted jobs stay within the budget and a slot is free; every job
+// count, alpha, rho) are submitted from any host thread and queued.  An
+// admitter thread creates queued jobs in arrival order while the device
+// bytes of the admitted jobs stay within the budget, a slot is free and the
+// admitted jobs do not already fill a tick; a worker thread runs the ticks.
+// Every job
 // keeps its whole state resident (stacks, consensus image, amplitudes).  One
 // tick runs one iteration of Algorithm 1 for every admitted job: one agent
 // launch per (probe size, amplitude format, plan) group, whose clusters
@@ -103,11 +105,17 @@ struct pmace_server {
     int64_t budget = 0;
     int32_t max_active = 0;
     int32_t tile_h = 16;
-    cudaStream_t stream = nullptr;
+    int64_t fill_pixels = 0;           // admit while the active jobs' window pixels per tick stay below this
+    cudaStream_t stream = nullptr;     // ticks and readouts
+    cudaStream_t admit_stream = nullptr;  // job creation, so admission does not wait for queued ticks
 
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_work, cv_done, cv_admit;
     std::deque<Request> queue;
+    std::vector<Active> ready;           // created by the admitter, not yet picked up by the worker
+    std::vector<pmace_job*> graveyard;   // retired jobs the admitter frees
+    int64_t committed_px = 0;            // window pixels per tick of created or creating jobs
+    int32_t committed_n = 0;             // jobs created or being created
     std::map<int64_t, Result> results;
     int64_t next_id = 1;
     int64_t used = 0;
@@ -115,7 +123,7 @@ struct pmace_server {
     int32_t n_active = 0;
     bool stop = false;
     std::string error;
-    std::thread worker;
+    std::thread worker, admitter;
 
     // worker-only state
     std::vector<Active> active;
@@ -125,7 +133,7 @@ struct pmace_server {
     DevBuf<int2> d_gwork;
 
     void run();
-    void admit();
+    void admit_loop();
     pmace_status tick();
     void retire_finished();
 };
@@ -158,19 +166,54 @@ void finish_with_error(pmace_server* sv, const Request& r, pmace_status st, cons
 
 }  // namespace
 
-// Admit queued jobs in arrival order while they fit the budget and a slot.
-void pmace_server::admit() {
+// Admitter thread: creates queued jobs in arrival order (on its own stream)
+// while they fit the budget, a slot and the fill target, and hands them to
+// the worker; it also frees retired jobs, so that neither creation nor the
+// device synchronisation of freeing ever stalls the worker's ticks.
+void pmace_server::admit_loop() {
+    cudaSetDevice(device);
     for (;;) {
         Request r;
+        std::vector<pmace_job*> dead;
+        int64_t px = 0;
         {
-            std::lock_guard<std::mutex> lock(mu);
-            if (queue.empty() || (int32_t)active.size() >= max_active) return;
-            const int64_t need = footprint(queue.front().dims, queue.front().fmt);
-            if (!active.empty() && used + need > budget) return;   // wait for memory to free up
-            r = std::move(queue.front());
-            queue.pop_front();
+            std::unique_lock<std::mutex> lock(mu);
+            for (;;) {
+                if (stop) break;
+                if (!graveyard.empty()) break;
+                if (!queue.empty() && committed_n < max_active) {
+                    const Request& f = queue.front();
+                    const int64_t need = footprint(f.dims, f.fmt);
+                    if (committed_n == 0 || (used + need <= budget && committed_px < fill_pixels)) break;
+                }
+                cv_admit.wait_for(lock, std::chrono::milliseconds(20));
+            }
+            if (stop) break;
+            dead.swap(graveyard);
+            if (!queue.empty() && committed_n < max_active) {
+                const Request& f = queue.front();
+                const int64_t need = footprint(f.dims, f.fmt);
+                if (committed_n == 0 || (used + need <= budget && committed_px < fill_pixels)) {
+                    r = std::move(queue.front());
+                    queue.pop_front();
+                    px = (int64_t)r.dims.J * r.dims.np * r.dims.np;
+                    committed_n++;
+                    committed_px += px;
+                    used += need;   // reserved until the job's real size is known
+                }
+            }
         }
-        if (footprint(r.dims, r.fmt) > budget) {
+        for (pmace_job* j : dead) pmace_destroy(j);
+        if (r.id == 0) continue;
+        const int64_t reserved = footprint(r.dims, r.fmt);
+        auto release = [&]() {
+            std::lock_guard<std::mutex> lock(mu);
+            committed_n--;
+            committed_px -= px;
+            used -= reserved;
+        };
+        if (reserved > budget) {
+            release();
             finish_with_error(this, r, PMACE_ERR_OOM, "job does not fit the server's device-memory budget");
             continue;
         }
@@ -178,19 +221,22 @@ void pmace_server::admit() {
         const double t0 = now_ms();
         pmace_status st = pmace_create(&r.dims, r.probe.data(), r.offsets.data(), r.amps.data(), r.fmt,
                                        r.scales.empty() ? nullptr : r.scales.data(),
-                                       r.init.empty() ? nullptr : r.init.data(), 0, stream, &job);
-        if (st != PMACE_OK) {
-            finish_with_error(this, r, st, pmace_last_error(nullptr));
-            continue;
-        }
-        if (job->tile_h != tile_h) {
-            st = pmace_set_plan(job, job->variant, tile_h, stream);
+                                       r.init.empty() ? nullptr : r.init.data(), 0, admit_stream, &job);
+        if (st == PMACE_OK && job->tile_h != tile_h) {
+            st = pmace_set_plan(job, job->variant, tile_h, admit_stream);
             if (st != PMACE_OK) {
                 const std::string msg = pmace_last_error(job);
                 pmace_destroy(job);
+                release();
                 finish_with_error(this, r, st, msg);
                 continue;
             }
+        }
+        if (st != PMACE_OK) {
+            const std::string msg = pmace_last_error(nullptr);
+            release();
+            finish_with_error(this, r, st, msg);
+            continue;
         }
         Active a;
         a.job = job;
@@ -204,9 +250,9 @@ void pmace_server::admit() {
         r.init.shrink_to_fit();
         a.req = std::move(r);
         std::lock_guard<std::mutex> lock(mu);
-        used += a.bytes;
-        active.push_back(std::move(a));
-        n_active = (int32_t)active.size();
+        used += a.bytes - reserved;
+        ready.push_back(std::move(a));
+        cv_work.notify_all();
     }
 }
 
@@ -301,16 +347,19 @@ void pmace_server::retire_finished() {
         res.status = pmace_get_image(a.job, res.image.data(), 0, stream);   // synchronises the stream
         if (res.status != PMACE_OK) res.error = pmace_last_error(a.job);
         res.finish_ms = now_ms();
-        pmace_destroy(a.job);
         {
             std::lock_guard<std::mutex> lock(mu);
             used -= a.bytes;
+            committed_n--;
+            committed_px -= (int64_t)a.job->dims.J * a.job->dims.np * a.job->dims.np;
+            graveyard.push_back(a.job);   // freed by the admitter thread
             results[a.req.id] = std::move(res);
             retired++;
             active.erase(active.begin() + i);
             n_active = (int32_t)active.size();
         }
         cv_done.notify_all();
+        cv_admit.notify_all();
     }
 }
 
@@ -320,32 +369,34 @@ void pmace_server::run() {
         {
             std::unique_lock<std::mutex> lock(mu);
             if (stop) break;
-            if (active.empty() && queue.empty()) {
+            if (active.empty() && ready.empty()) {
                 cv_work.wait_for(lock, std::chrono::milliseconds(20));
                 continue;
             }
+            for (Active& a : ready) active.push_back(std::move(a));
+            ready.clear();
+            n_active = (int32_t)active.size();
         }
-        admit();
-        if (active.empty()) continue;
         // jobs admitted with zero iterations retire at once
         pmace_status st = tick();
         if (st != PMACE_OK) {
             // a launch failed: fail every active job and keep serving the queue
-            for (Active& a : active) {
-                finish_with_error(this, a.req, st, error);
-                pmace_destroy(a.job);
-            }
+            for (Active& a : active) finish_with_error(this, a.req, st, error);
             std::lock_guard<std::mutex> lock(mu);
+            for (Active& a : active) {
+                used -= a.bytes;
+                committed_n--;
+                committed_px -= (int64_t)a.job->dims.J * a.job->dims.np * a.job->dims.np;
+                graveyard.push_back(a.job);
+            }
             active.clear();
-            used = 0;
             n_active = 0;
             cudaGetLastError();
+            cv_admit.notify_all();
             continue;
         }
         retire_finished();
     }
-    for (Active& a : active) pmace_destroy(a.job);
-    active.clear();
 }
 
 extern "C" {
@@ -367,13 +418,16 @@ pmace_status pmace_server_create(const pmace_server_config* cfg, pmace_server_ha
     sv->max_active = (cfg && cfg->max_active_jobs > 0) ? cfg->max_active_jobs : 64;
     const int th = cfg ? cfg->tile_h : 0;
     sv->tile_h = (th == 8 || th == 16 || th == 32) ? th : 16;
+    sv->fill_pixels = (cfg && cfg->fill_pixels > 0) ? cfg->fill_pixels : ((int64_t)1 << 27);
     e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->admit_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete sv;
         set_unbound_error(cudaGetErrorString(e));
         return PMACE_ERR_CUDA;
     }
     sv->worker = std::thread([sv] { sv->run(); });
+    sv->admitter = std::thread([sv] { sv->admit_loop(); });
     *out = sv;
     return PMACE_OK;
 }
@@ -403,7 +457,7 @@ pmace_status pmace_server_submit(pmace_server_handle sv, const pmace_request* re
     r.id = sv->next_id++;
     *id = r.id;
     sv->queue.push_back(std::move(r));
-    sv->cv_work.notify_all();
+    sv->cv_admit.notify_all();
     return PMACE_OK;
 }
 
@@ -473,12 +527,18 @@ void pmace_server_destroy(pmace_server_handle sv) {
         std::lock_guard<std::mutex> lock(sv->mu);
         sv->stop = true;
         sv->cv_work.notify_all();
+        sv->cv_admit.notify_all();
     }
     if (sv->worker.joinable()) sv->worker.join();
+    if (sv->admitter.joinable()) sv->admitter.join();
+    for (Active& a : sv->active) pmace_destroy(a.job);
+    for (Active& a : sv->ready) pmace_destroy(a.job);
+    for (pmace_job* j : sv->graveyard) pmace_destroy(j);
     cudaStreamSynchronize(sv->stream);
-    cudaStream_t s = sv->stream;
+    cudaStream_t s = sv->stream, s2 = sv->admit_stream;
     delete sv;   // frees the launch tables
     cudaStreamDestroy(s);
+    cudaStreamDestroy(s2);
 }
 
 }  // extern "C"

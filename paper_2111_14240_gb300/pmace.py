@@ -51,7 +51,7 @@ class pmace_plan(ctypes.Structure):
 
 class pmace_server_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_active_jobs", ctypes.c_int32),
-                ("tile_h", ctypes.c_int32)]
+                ("tile_h", ctypes.c_int32), ("fill_pixels", ctypes.c_int64)]
 
 
 class pmace_request(ctypes.Structure):
@@ -358,8 +358,9 @@ class Server:
     """Continuous-batching server (pmace_server_*): jobs are submitted with
     host arrays and read back as host images."""
 
-    def __init__(self, hbm_budget_bytes=0, max_active_jobs=0, tile_h=0):
-        cfg = pmace_server_config(int(hbm_budget_bytes), int(max_active_jobs), int(tile_h))
+    def __init__(self, hbm_budget_bytes=0, max_active_jobs=0, tile_h=0, fill_pixels=0):
+        cfg = pmace_server_config(int(hbm_budget_bytes), int(max_active_jobs), int(tile_h),
+                                  int(fill_pixels))
         self.h = ctypes.c_void_p()
         _check(_lib.pmace_server_create(ctypes.byref(cfg), ctypes.byref(self.h)), None)
         self.shapes = {}
