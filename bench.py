@@ -124,15 +124,38 @@ class ClockSampler:
 
 
 def dist_setup():
+    """One process per GPU under torchrun (RANK/LOCAL_RANK/WORLD_SIZE/MASTER_*
+    from the environment).  NCCL when CUDA is available, else gloo;
+    PMACE_DIST_BACKEND overrides.  Returns (dist or None, world, rank, local)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
-        dist.init_process_group(backend=backend)
+        backend = os.environ.get("PMACE_DIST_BACKEND") or ("nccl" if torch.cuda.is_available() else "gloo")
+        if not dist.is_initialized():
+            dist.init_process_group(backend=backend)
         return dist, world, rank, local
     return None, 1, 0, local
+
+
+def max_over_ranks(dist, values):
+    """Element-wise maximum of a list of floats over all ranks (identity
+    without a process group); the only collective of the benchmark."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def weak_scaling_value(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput: every rank processes the same work (replicas),
+    timed by the slowest rank."""
+    return world * units_per_rank / seconds
 
 
 def measured_peaks():
@@ -184,6 +207,8 @@ def run_reference(args):
     J = w.J
     budget = 150.0
     per_step = max(0.2, min(6.0, budget / max(1, args.steps + args.warmup)))
+    if args.ref_seconds > 0:
+        per_step = args.ref_seconds
     from oracle import pmace_oracle as orc
     probe, offs, y = w.probe, w.offsets, w.y
     m0 = 8
@@ -272,14 +297,11 @@ def run_ours(args):
     h2d = y32.nbytes + probe32.nbytes + w.offsets.nbytes
     d2h = img_pin.numel() * 4 + 16
 
-    if dist:
-        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_s = float(t[0]), float(t[1])
+    ms, e2e_s = max_over_ranks(dist, [ms, e2e_s])
     if rank != 0:
         return 0
 
-    value = world * J * args.steps / (ms / 1e3)
+    value = weak_scaling_value(world, J * args.steps, ms / 1e3)
     peak, peak_kind = measured_peaks()
     agent_avg_ms = kt["agent_ms"] / max(1, kt["agent_launches"])
     cons_avg_ms = kt["consensus_ms"] / max(1, kt["consensus_launches"])
@@ -306,7 +328,7 @@ def run_ours(args):
         "residual": {"r_fp": r_fp, "r_data": r_data},
         "gpu_launches": 2 * args.steps,
         "clocks": clocks.summary(),
-        "e2e": {"value": world * J * args.steps / e2e_s, "unit": UNIT,
+        "e2e": {"value": weak_scaling_value(world, J * args.steps, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "note": "one whole job through the C ABI from pinned host memory: create + K "
                         "iterations + residual + image readback; bytes amortised over K"},
@@ -431,6 +453,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=0.0,
+                    help="reference arm: seconds of oracle work per step (0: sized for a few minutes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
     ap.add_argument("--serve-jobs", type=int, default=256)
