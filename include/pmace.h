@@ -24,7 +24,10 @@
  *    PMACE_OK leaves the handle valid unless documented otherwise.
  *  - the library runs on the CUDA device that is current when pmace_create
  *    is called; later calls on the handle must be made with that device
- *    current.
+ *    current;
+ *  - calls on one handle must follow one another on the GPU (one stream, or
+ *    streams the caller synchronises): they share the job's stacks and the
+ *    consensus gather's scratch partial sums and tile counters.
  */
 #ifndef PMACE_H
 #define PMACE_H

@@ -27,13 +27,20 @@ struct pmace_job {
     pmace::AgentPlanInfo plan{};
     int tiles_x = 0, tiles_y = 0, ntiles = 0;
     int tile_h = 16;          // gather tile height (rows), width kGatherTileW
+    int nunits = 0;           // gather CTAs (tiles with long lists are split)
+    int gblock = 0;           // gather block length B: units split lists at multiples of B
+    int nslots = 0;           // scratch slots of split tiles
 
     float2 *q = nullptr, *u = nullptr, *xbar = nullptr, *probe = nullptr, *dinv = nullptr,
            *tw = nullptr, *img_tmp = nullptr;
     void* y = nullptr;
     float *yscale = nullptr, *laminv = nullptr, *wk = nullptr;
     int2* offs = nullptr;
-    int *tile_ptr = nullptr, *tile_list = nullptr, *err = nullptr;
+    int *tile_list = nullptr, *gcounters = nullptr, *err = nullptr;
+    int4* units = nullptr;
+    int2* tile_seg = nullptr;
+    float2* gscratch = nullptr;
+    int64_t gather_bytes = 0; // device bytes of the gather tables, included in `bytes`
     double *partials = nullptr, *red_out = nullptr;
     int64_t bytes = 0;
 

@@ -133,17 +133,27 @@ std::vector<int> radices_of(int L) {
     return v;
 }
 
-// For every h->tile_h x kGatherTileW image tile, the ascending list of the
-// windows that intersect it (CSR: cnt[t]..cnt[t+1] index list); sets the
-// tile counts of h.
-void overlap_lists(pmace_job* h, const std::vector<int32_t>& offs_h, std::vector<int>& cnt,
-                   std::vector<int>& list) {
-    const int np = h->dims.np, J = h->dims.J;
-    const int TH = h->tile_h, TW = kGatherTileW;
-    h->tiles_y = (h->dims.n1 + TH - 1) / TH;
-    h->tiles_x = (h->dims.n2 + TW - 1) / TW;
-    h->ntiles = h->tiles_x * h->tiles_y;
-    cnt.assign(h->ntiles + 1, 0);
+// Gather tables of one tile height: for every tile_h x kGatherTileW image
+// tile the ascending list of the windows that intersect it (CSR: cnt[t] ..
+// cnt[t + 1]), cut into units where the window index crosses a multiple of
+// the job's block length B (windows [kB, (k+1)B) of the list form one
+// unit).  Every pixel's sum is then the ascending-block sum of per-block
+// partial sums, whatever the tile shape, so a job's results do not depend
+// on the gather tile height.
+struct GatherTables {
+    int tile_h = 16, tiles_x = 0, tiles_y = 0, ntiles = 0, nslots = 0;
+    std::vector<int> cnt, list;
+    std::vector<int4> units;   // (tile, lb, le, slot or -1)
+    std::vector<int2> seg;     // (first slot or -1, units) per tile
+};
+
+void overlap_lists(const pmace_dims& d, const std::vector<int32_t>& offs_h, GatherTables& t) {
+    const int np = d.np, J = d.J;
+    const int TH = t.tile_h, TW = kGatherTileW;
+    t.tiles_y = (d.n1 + TH - 1) / TH;
+    t.tiles_x = (d.n2 + TW - 1) / TW;
+    t.ntiles = t.tiles_x * t.tiles_y;
+    t.cnt.assign(t.ntiles + 1, 0);
     auto tile_range = [&](int j, int& y0, int& y1, int& x0, int& x1) {
         const int r = offs_h[2 * j], c = offs_h[2 * j + 1];
         y0 = r / TH;
@@ -155,17 +165,149 @@ void overlap_lists(pmace_job* h, const std::vector<int32_t>& offs_h, std::vector
         int y0, y1, x0, x1;
         tile_range(j, y0, y1, x0, x1);
         for (int ty = y0; ty <= y1; ++ty)
-            for (int tx = x0; tx <= x1; ++tx) cnt[ty * h->tiles_x + tx + 1]++;
+            for (int tx = x0; tx <= x1; ++tx) t.cnt[ty * t.tiles_x + tx + 1]++;
     }
-    for (int t = 0; t < h->ntiles; ++t) cnt[t + 1] += cnt[t];
-    list.assign(std::max(cnt[h->ntiles], 1), 0);
-    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (int k = 0; k < t.ntiles; ++k) t.cnt[k + 1] += t.cnt[k];
+    t.list.assign(std::max(t.cnt[t.ntiles], 1), 0);
+    std::vector<int> fill(t.cnt.begin(), t.cnt.end() - 1);
     for (int j = 0; j < J; ++j) {   // ascending j, so every list is ascending
         int y0, y1, x0, x1;
         tile_range(j, y0, y1, x0, x1);
         for (int ty = y0; ty <= y1; ++ty)
-            for (int tx = x0; tx <= x1; ++tx) list[fill[ty * h->tiles_x + tx]++] = j;
+            for (int tx = x0; tx <= x1; ++tx) t.list[fill[ty * t.tiles_x + tx]++] = j;
     }
+}
+
+// Units of the tables' lists for block length B (empty tiles keep one unit).
+int64_t count_units(const GatherTables& t, int B) {
+    int64_t n = 0;
+    for (int k = 0; k < t.ntiles; ++k) {
+        int64_t runs = 1;
+        for (int a = t.cnt[k] + 1; a < t.cnt[k + 1]; ++a) runs += t.list[a] / B != t.list[a - 1] / B;
+        n += runs;
+    }
+    return n;
+}
+
+void cut_units(GatherTables& t, int B) {
+    t.seg.resize(t.ntiles);
+    t.units.clear();
+    t.units.reserve(t.ntiles);
+    t.nslots = 0;
+    for (int k = 0; k < t.ntiles; ++k) {
+        const int lb = t.cnt[k], le = t.cnt[k + 1];
+        const size_t first = t.units.size();
+        int a = lb;
+        do {
+            int b = a + 1;
+            while (b < le && t.list[b] / B == t.list[a] / B) ++b;
+            t.units.push_back(make_int4(k, a, std::min(b, le), -1));
+            a = b;
+        } while (a < le);
+        const int ns = (int)(t.units.size() - first);
+        if (ns == 1) {
+            t.seg[k] = make_int2(-1, 1);
+        } else {
+            t.seg[k] = make_int2(t.nslots, ns);
+            for (int u = 0; u < ns; ++u) t.units[first + u].w = t.nslots + u;
+            t.nslots += ns;
+        }
+    }
+}
+
+// Gather CTAs per launch the block length aims for: enough to fill the GPU
+// several times over even when the image has few tiles, so that the long
+// lists of interior tiles do not set the launch's duration.
+constexpr int64_t kGatherTargetUnits = 3072;
+// Fewest windows per unit on average the block length allows.
+constexpr int64_t kGatherMinWindows = 16;
+
+// The job's block length B: the smallest B whose cut of the 16-row tiles'
+// lists gives at most max(tiles, min(kGatherTargetUnits, windows /
+// kGatherMinWindows)) units (PMACE_GATHER_UNITS and PMACE_GATHER_SEG, if
+// set, replace the two constants); J when the image alone has that many
+// tiles.  A function of the job's scan alone.
+int gather_block_length(const pmace_dims& d, const std::vector<int32_t>& offs_h) {
+    GatherTables t;
+    t.tile_h = 16;
+    overlap_lists(d, offs_h, t);
+    int64_t minw = kGatherMinWindows, units = kGatherTargetUnits;
+    if (const char* env = std::getenv("PMACE_GATHER_SEG")) {
+        const int v = std::atoi(env);
+        if (v > 0) minw = v;
+    }
+    if (const char* env = std::getenv("PMACE_GATHER_UNITS")) {
+        const int v = std::atoi(env);
+        if (v > 0) units = v;
+    }
+    const int64_t total = t.cnt[t.ntiles];
+    const int64_t target = std::max<int64_t>(t.ntiles, std::min<int64_t>(units, total / minw));
+    if (t.ntiles >= target) return std::max(d.J, 1);
+    int lo = 1, hi = std::max(d.J, 1);   // count_units(hi) = ntiles <= target
+    while (lo < hi) {
+        const int mid = lo + (hi - lo) / 2;
+        if (count_units(t, mid) <= target) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+GatherTables make_gather_tables(const pmace_dims& d, const std::vector<int32_t>& offs_h, int tile_h, int B) {
+    GatherTables t;
+    t.tile_h = tile_h;
+    overlap_lists(d, offs_h, t);
+    cut_units(t, B);
+    return t;
+}
+
+// Build the gather tables for tile height tile_h, upload them, and replace
+// the job's current ones (freed after `s` has been synchronised).
+pmace_status install_gather_tables(pmace_job* h, int tile_h, cudaStream_t s) {
+    if (h->gblock <= 0) h->gblock = gather_block_length(h->dims, h->offs_host);
+    const GatherTables t = make_gather_tables(h->dims, h->offs_host, tile_h, h->gblock);
+    int* list = nullptr;
+    int4* units = nullptr;
+    int2* seg = nullptr;
+    float2* scratch = nullptr;
+    int* counters = nullptr;
+    const size_t slot = (size_t)tile_h * kGatherTileW;
+    const size_t b_list = t.list.size() * sizeof(int), b_units = t.units.size() * sizeof(int4),
+                 b_seg = t.seg.size() * sizeof(int2),
+                 b_scr = std::max<size_t>((size_t)t.nslots * slot, 1) * sizeof(float2),
+                 b_cnt = (size_t)t.ntiles * sizeof(int);
+    cudaError_t e = cudaMalloc(&list, b_list);
+    if (e == cudaSuccess) e = cudaMalloc(&units, b_units);
+    if (e == cudaSuccess) e = cudaMalloc(&seg, b_seg);
+    if (e == cudaSuccess) e = cudaMalloc(&scratch, b_scr);
+    if (e == cudaSuccess) e = cudaMalloc(&counters, b_cnt);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(list, t.list.data(), b_list, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(units, t.units.data(), b_units, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(seg, t.seg.data(), b_seg, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, b_cnt, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host tables die on return
+    if (e != cudaSuccess) {
+        for (void* p : {(void*)list, (void*)units, (void*)seg, (void*)scratch, (void*)counters})
+            if (p) cudaFree(p);
+        return cuda_fail(h, e, "gather tables");
+    }
+    for (void* p : {(void*)h->tile_list, (void*)h->units, (void*)h->tile_seg, (void*)h->gscratch,
+                    (void*)h->gcounters})
+        if (p) cudaFree(p);
+    const int64_t bytes = (int64_t)(b_list + b_units + b_seg + b_scr + b_cnt);
+    h->bytes += bytes - h->gather_bytes;
+    h->gather_bytes = bytes;
+    h->tile_list = list;
+    h->units = units;
+    h->tile_seg = seg;
+    h->gscratch = scratch;
+    h->gcounters = counters;
+    h->tile_h = t.tile_h;
+    h->tiles_x = t.tiles_x;
+    h->tiles_y = t.tiles_y;
+    h->ntiles = t.ntiles;
+    h->nunits = (int)t.units.size();
+    h->nslots = t.nslots;
+    return PMACE_OK;
 }
 
 pmace_status build_tables(pmace_job* h, const std::vector<float>& probe_h,
@@ -195,9 +337,6 @@ pmace_status build_tables(pmace_job* h, const std::vector<float>& probe_h,
         const double ang = -2.0 * M_PI * (double)m / (double)np;
         tw[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
-    // scan-overlap lists: for every gather tile the ascending list of windows that intersect it
-    std::vector<int> cnt, list;
-    overlap_lists(h, offs_h, cnt, list);
     // row and column spectrum orders of the agent kernel: the two in-place
     // row stages leave each row digit-reversed; along columns, local row k2
     // of CTA `rank` holds frequency rank + cluster * k2 after the cross-CTA
@@ -210,8 +349,6 @@ pmace_status build_tables(pmace_job* h, const std::vector<float>& probe_h,
     PM_CUDA(h, dalloc(h, &h->tw, (size_t)np));
     PM_CUDA(h, dalloc(h, &h->wk, P));
     PM_CUDA(h, dalloc(h, &h->offs, (size_t)J));
-    PM_CUDA(h, dalloc(h, &h->tile_ptr, (size_t)h->ntiles + 1));
-    PM_CUDA(h, dalloc(h, &h->tile_list, list.size()));
     auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
         keep.emplace_back((const char*)src, (const char*)src + bytes);   // alive until the sync
         return cudaMemcpyAsync(dst, keep.back().data(), bytes, cudaMemcpyHostToDevice, s);
@@ -221,8 +358,6 @@ pmace_status build_tables(pmace_job* h, const std::vector<float>& probe_h,
     PM_CUDA(h, up(h->tw, tw.data(), np * sizeof(float2)));
     PM_CUDA(h, up(h->wk, wk.data(), P * sizeof(float)));
     PM_CUDA(h, up(h->offs, offs_h.data(), (size_t)J * 2 * sizeof(int32_t)));
-    PM_CUDA(h, up(h->tile_ptr, cnt.data(), cnt.size() * sizeof(int)));
-    PM_CUDA(h, up(h->tile_list, list.data(), list.size() * sizeof(int)));
     // permutation tables (row order, then column order) live only until the amplitude pass
     PM_CUDA(h, cudaMalloc(perm_out, 2 * np * sizeof(int)));
     std::vector<int> both(rowperm);
@@ -235,8 +370,8 @@ pmace_status build_tables(pmace_job* h, const std::vector<float>& probe_h,
 void free_job(pmace_job* h) {
     if (!h) return;
     void* ptrs[] = {h->q, h->u, h->xbar, h->probe, h->dinv, h->tw, h->img_tmp, h->y, h->yscale,
-                    h->laminv, h->wk, h->offs, h->tile_ptr, h->tile_list, h->err, h->partials,
-                    h->red_out};
+                    h->laminv, h->wk, h->offs, h->tile_list, h->units, h->tile_seg, h->gscratch,
+                    h->gcounters, h->err, h->partials, h->red_out};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto* v : {&h->ev_agent, &h->ev_cons})
@@ -277,8 +412,11 @@ GatherArgs gather_args(const pmace_job* h) {
     GatherArgs g{};
     g.wk = h->wk;
     g.offs = h->offs;
-    g.tile_ptr = h->tile_ptr;
     g.tile_list = h->tile_list;
+    g.units = h->units;
+    g.tile_seg = h->tile_seg;
+    g.scratch = h->gscratch;
+    g.counters = h->gcounters;
     g.laminv = h->laminv;
     g.n1 = h->dims.n1;
     g.n2 = h->dims.n2;
@@ -324,7 +462,7 @@ pmace_status launch_iteration(pmace_job* h, float alpha, float rho, cudaStream_t
         PM_CUDA(h, record_pair(h->ev_agent, h->n_agent, false, s));
         PM_CUDA(h, record_pair(h->ev_cons, h->n_cons, true, s));
     }
-    PM_CUDA(h, launch_gather_consensus(g, h->ntiles, h->tile_h, s));
+    PM_CUDA(h, launch_gather_consensus(g, h->nunits, h->tile_h, s));
     if (events) PM_CUDA(h, record_pair(h->ev_cons, h->n_cons, false, s));
     h->rho_pending = rho;
     h->iterations++;
@@ -403,24 +541,8 @@ pmace_status switch_plan(pmace_job* h, int variant, int tile_h, cudaStream_t s) 
         h->plan = info;
     }
     if (tile_h != h->tile_h) {
-        h->tile_h = tile_h;
-        std::vector<int> cnt, list;
-        overlap_lists(h, h->offs_host, cnt, list);
-        int *tp = nullptr, *tl = nullptr;
-        cudaError_t e = cudaMalloc(&tp, cnt.size() * sizeof(int));
-        if (e == cudaSuccess) e = cudaMalloc(&tl, list.size() * sizeof(int));
-        if (e == cudaSuccess) e = cudaMemcpy(tp, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(tl, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            if (tp) cudaFree(tp);
-            if (tl) cudaFree(tl);
-            return cuda_fail(h, e, "overlap lists");
-        }
-        cudaStreamSynchronize(s);
-        cudaFree(h->tile_ptr);
-        cudaFree(h->tile_list);
-        h->tile_ptr = tp;
-        h->tile_list = tl;
+        const pmace_status st = install_gather_tables(h, tile_h, s);
+        if (st != PMACE_OK) return st;
     }
     if (h->graph) {   // the captured launches refer to the old plan
         cudaGraphExecDestroy(h->graph);
@@ -547,6 +669,7 @@ pmace_status pmace_create(const pmace_dims* dims, const float* probe, const int3
         return bail(st2);
     };
     pmace_status st = build_tables(h, probe_h, offs_h, s, keep, &perm_d);
+    if (st == PMACE_OK) st = install_gather_tables(h, h->tile_h, s);
     if (st != PMACE_OK) return bail_perm(st);
 
     cudaError_t e;
@@ -586,7 +709,7 @@ pmace_status pmace_create(const pmace_dims* dims, const float* probe, const int3
     // weight image Lambda^-1
     GatherArgs g = gather_args(h);
     g.lam_out = h->laminv;
-    PM_CREATE(launch_gather_weights(g, h->ntiles, h->tile_h, s));
+    PM_CREATE(launch_gather_weights(g, h->nunits, h->tile_h, s));
 
     // initial stacks
     double sumsq = 0.0;
@@ -762,7 +885,7 @@ pmace_status pmace_get_image(pmace_handle h, float* out, int out_on_device, void
     g.xbar_in = h->xbar;
     g.out = dst;
     g.two_rho = 2.0f * h->rho_pending;
-    PM_CUDA(h, launch_gather_readout(g, h->ntiles, h->tile_h, s));
+    PM_CUDA(h, launch_gather_readout(g, h->nunits, h->tile_h, s));
     if (!out_on_device) {
         PM_CUDA(h, cudaMemcpyAsync(out, dst, NI * sizeof(float2), cudaMemcpyDeviceToHost, s));
         PM_CUDA(h, cudaStreamSynchronize(s));

@@ -45,8 +45,11 @@ struct GatherArgs {
     const float2* src;      // [J][Np][Np] stack to average (u or q)
     const float* wk;        // [Np][Np] |d|^kappa
     const int2* offs;       // [J]
-    const int* tile_ptr;    // [ntiles + 1] CSR row pointers
-    const int* tile_list;   // patch indices per tile, ascending
+    const int* tile_list;   // patch indices per tile, ascending, tiles one after another
+    const int4* units;      // [nunits] CTA k: (tile, lb, le, slot), windows tile_list[lb..le)
+    const int2* tile_seg;   // [ntiles] (first scratch slot, CTAs) of every tile
+    float2* scratch;        // [nslots][tile_h * kGatherTileW] partial sums of split tiles
+    int* counters;          // [ntiles] CTAs of a split tile finished; 0 between launches
     const float* laminv;    // [n1][n2] Lambda^-1 (0 where Lambda = 0)
     const float2* xbar_in;  // readout: consensus image
     float2* out;            // [n1][n2]
@@ -60,6 +63,15 @@ struct GatherArgs {
 // kGatherRowsPerThread rows of its column, so a tile has tile_h * 8 threads.
 constexpr int kGatherTileW = 32;
 constexpr int kGatherRowsPerThread = 4;
+// A tile's ascending window list is gathered by one CTA ("unit") per run
+// of windows with the same index block i / B (B is fixed per job), so
+// interior tiles with long lists are spread over several CTAs.  Unit
+// `slot` >= 0 writes its partial sums to scratch slot `slot`; the unit that
+// finishes last (a counter per tile) adds the tile's partials in ascending
+// block order, so the sum order is fixed by the tables, not by timing.
+// slot = -1: the tile has one unit, which writes the result.
+// Windows of a unit are staged in shared memory kGatherStage at a time.
+constexpr int kGatherStage = 64;
 __host__ __device__ constexpr int gather_threads(int tile_h) {
     return tile_h / kGatherRowsPerThread * kGatherTileW;
 }
@@ -105,13 +117,14 @@ cudaError_t agent_entry_batched_128(const AgentArgs* descs, const int2* work, in
 cudaError_t agent_entry_batched_256(const AgentArgs* descs, const int2* work, int nclusters, int v, int amp_f16, cudaStream_t s);
 
 // Support kernels (support.cu).
-cudaError_t launch_gather_weights(const GatherArgs& g, int ntiles, int tile_h, cudaStream_t s);
-cudaError_t launch_gather_consensus(const GatherArgs& g, int ntiles, int tile_h, cudaStream_t s);
-cudaError_t launch_gather_readout(const GatherArgs& g, int ntiles, int tile_h, cudaStream_t s);
+// nunits CTAs, one per entry of g.units.
+cudaError_t launch_gather_weights(const GatherArgs& g, int nunits, int tile_h, cudaStream_t s);
+cudaError_t launch_gather_consensus(const GatherArgs& g, int nunits, int tile_h, cudaStream_t s);
+cudaError_t launch_gather_readout(const GatherArgs& g, int nunits, int tile_h, cudaStream_t s);
 // Consensus of several jobs in one launch: `work` (device) holds the
-// (job, tile) pair of each of the ntiles CTAs, `descs` (device) each job's
+// (job, unit) pair of each of the nunits CTAs, `descs` (device) each job's
 // arguments; every job uses the same tile height.
-cudaError_t launch_gather_consensus_batched(const GatherArgs* descs, const int2* work, int ntiles, int tile_h,
+cudaError_t launch_gather_consensus_batched(const GatherArgs* descs, const int2* work, int nunits, int tile_h,
                                             cudaStream_t s);
 cudaError_t launch_prep_amps(const void* amps_in, int amp_f16, const float* scales, void* y_out,
                              const int* rowperm, const int* colperm, int J, int np,

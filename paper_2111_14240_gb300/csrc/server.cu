@@ -75,8 +75,13 @@ struct Result {
 // Device bytes a job will hold (stacks, amplitudes, images and tables).
 int64_t footprint(const pmace_dims& d, pmace_amp_format fmt) {
     const int64_t P = (int64_t)d.np * d.np, JP = (int64_t)d.J * P, NI = (int64_t)d.n1 * d.n2;
+    // gather scratch: one slot of at most 32 x 32 pixels per unit of a split
+    // tile; the block length keeps the units near 3072 (a little over, where
+    // the 8- and 32-row tiles cut differently than the 16-row ones)
+    const int64_t per_window = (int64_t)(d.np / 8 + 2) * (d.np / 32 + 2);
+    const int64_t slots = std::min<int64_t>(8192, (int64_t)d.J * per_window / 8);
     return JP * 16 + JP * (fmt == PMACE_AMP_F16_SCALED ? 2 : 4) + NI * (8 + 4 + 8) + P * 24 +
-           (int64_t)d.J * (16 * 4 * 8 + 8 + 4) + NI / 64 * 8 + (1 << 20);
+           (int64_t)d.J * (16 * 4 * 8 + 8 + 4) + NI / 64 * 8 + slots * 32 * 32 * 8 + (1 << 20);
 }
 
 template <typename T>
@@ -296,7 +301,7 @@ pmace_status pmace_server::tick() {
         g.out = h->xbar;
         const int gd = (int)gdesc.size();
         gdesc.push_back(g);
-        for (int t = 0; t < h->ntiles; ++t) gwork.push_back(make_int2(gd, t));
+        for (int t = 0; t < h->nunits; ++t) gwork.push_back(make_int2(gd, t));
     }
     cudaError_t e = d_adesc.reserve(adesc.size());
     if (e == cudaSuccess) e = d_awork.reserve(awork.size());

@@ -9,20 +9,34 @@
 namespace pmace {
 
 // ---------------------------------------------------------------------------
-// Pixel-owner gather over the scan-overlap lists.  One CTA owns a
-// TH x kGatherTileW block of image pixels and walks the ascending
-// list of windows that intersect it; every pixel sums
-// |d(p - o_i)|^kappa * src_i(p - o_i) over the windows i that contain it in
-// ascending i, so the result is deterministic and needs no atomics.
+// Pixel-owner gather over the scan-overlap lists.  The image is cut into
+// TH x kGatherTileW tiles; every tile has the ascending list of the windows
+// that intersect it, cut into runs ("units", one CTA each) of windows of the
+// same index block i / B.  Every pixel sums |d(p - o_i)|^kappa * src_i(p - o_i)
+// over the windows i that contain it, in ascending i within a block and then
+// over the blocks in ascending order (a block with no such window adds an
+// exact 0), so the result is deterministic, the same for every tile height,
+// and needs no float atomics.
 //   MODE 0: Lambda = sum_i |d|^kappa (FP64), writes Lambda^-1 (0 where Lambda = 0)
 //   MODE 1: xbar = Lambda^-1 sum_i P_i^t |D|^kappa u_i                 (G, S6)
 //   MODE 2: x_hat = Lambda^-1 sum_i P_i^t |D|^kappa q_i + 2 rho xbar   (readout)
+// A tile cut into several units: each unit stores its partial sums in its
+// scratch slot, fences, and counts itself in the tile's counter; the unit
+// that brings the counter to the tile's unit count resets it to 0, reads
+// the slots back from L2 in ascending order and writes the pixels.
 // ---------------------------------------------------------------------------
 template <int MODE, int TH>
-__device__ __forceinline__ void gather_body(const GatherArgs& g, const int tile) {
+__device__ __forceinline__ void gather_body(const GatherArgs& g, const int unit) {
     constexpr int TW = kGatherTileW;
     constexpr int NT = gather_threads(TH);
     constexpr int RPT = kGatherRowsPerThread;       // rows per thread
+    static_assert(NT >= kGatherStage, "one thread stages one window of a chunk");
+    __shared__ int s_i[kGatherStage];
+    __shared__ int2 s_o[kGatherStage];
+    __shared__ int s_last;
+
+    const int4 un = __ldg(g.units + unit);          // (tile, lb, le, slot)
+    const int tile = un.x;
     const int ty0 = (tile / g.tiles_x) * TH, tx0 = (tile % g.tiles_x) * TW;
     const int lane = threadIdx.x % TW, grp = threadIdx.x / TW;
     const int px = tx0 + lane;
@@ -36,44 +50,84 @@ __device__ __forceinline__ void gather_body(const GatherArgs& g, const int tile)
         if constexpr (MODE == 0) acc[r] = 0.0;
         else acc[r] = make_float2(0.f, 0.f);
     }
-    const int lb = g.tile_ptr[tile], le = g.tile_ptr[tile + 1];
-    // Windows are taken U at a time so that U * RPT loads are in flight per
-    // thread; the accumulation still runs over ascending window index.
-    constexpr int U = 4;
-    for (int li = lb; li < le; li += U) {
-        float wgt[U][RPT];
-        float2 val[U][RPT];
+    for (int cb = un.y; cb < un.z; cb += kGatherStage) {
+        const int n = min(kGatherStage, un.z - cb);
+        if (cb != un.y) __syncthreads();            // the previous chunk is consumed
+        if (threadIdx.x < n) {
+            const int i = __ldg(g.tile_list + cb + threadIdx.x);
+            s_i[threadIdx.x] = i;
+            s_o[threadIdx.x] = __ldg(g.offs + i);
+        }
+        __syncthreads();
+        // Windows are taken U at a time so that U * RPT loads are in flight
+        // per thread; the accumulation still runs over ascending window index.
+        constexpr int U = 4;
+        for (int k0 = 0; k0 < n; k0 += U) {
+            float wgt[U][RPT];
+            float2 val[U][RPT];
 #pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const bool have = li + k < le;
-            const int i = have ? __ldg(g.tile_list + li + k) : 0;
-            const int2 o = have ? __ldg(g.offs + i) : make_int2(-(1 << 29), -(1 << 29));
-            const int lx = px - o.y;
-            const bool inx = have && (unsigned)lx < (unsigned)np;
+            for (int k = 0; k < U; ++k) {
+                const bool have = k0 + k < n;
+                const int i = have ? s_i[k0 + k] : 0;
+                const int2 o = have ? s_o[k0 + k] : make_int2(-(1 << 29), -(1 << 29));
+                const int lx = px - o.y;
+                const bool inx = have && (unsigned)lx < (unsigned)np;
 #pragma unroll
-            for (int r = 0; r < RPT; ++r) {
-                const int py = ty0 + grp + r * (NT / TW);
-                const int ly = py - o.x;
-                wgt[k][r] = 0.f;
-                val[k][r] = make_float2(0.f, 0.f);
-                if (inx && (unsigned)ly < (unsigned)np) {
-                    const int e = ly * np + lx;
-                    wgt[k][r] = __ldg(g.wk + e);
-                    if constexpr (MODE != 0) val[k][r] = __ldg(g.src + (size_t)i * P + e);
+                for (int r = 0; r < RPT; ++r) {
+                    const int py = ty0 + grp + r * (NT / TW);
+                    const int ly = py - o.x;
+                    wgt[k][r] = 0.f;
+                    val[k][r] = make_float2(0.f, 0.f);
+                    if (inx && (unsigned)ly < (unsigned)np) {
+                        const int e = ly * np + lx;
+                        wgt[k][r] = __ldg(g.wk + e);
+                        if constexpr (MODE != 0) val[k][r] = __ldg(g.src + (size_t)i * P + e);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    if (wgt[k][r] != 0.f) {
+                        if constexpr (MODE == 0) {
+                            acc[r] += (double)wgt[k][r];
+                        } else {
+                            acc[r].x = fmaf(wgt[k][r], val[k][r].x, acc[r].x);
+                            acc[r].y = fmaf(wgt[k][r], val[k][r].y, acc[r].y);
+                        }
+                    }
                 }
             }
         }
+    }
+    if (un.w >= 0) {                                 // tile split over several units
+        Acc* mine = reinterpret_cast<Acc*>(g.scratch) + (size_t)un.w * (TH * TW);
 #pragma unroll
-        for (int k = 0; k < U; ++k) {
+        for (int r = 0; r < RPT; ++r) mine[r * NT + threadIdx.x] = acc[r];
+        __threadfence();
+        __syncthreads();
+        const int2 ts = __ldg(g.tile_seg + tile);    // (first slot, units)
+        if (threadIdx.x == 0) {
+            const int done = atomicAdd(g.counters + tile, 1);
+            s_last = done == ts.y - 1;
+            if (s_last) g.counters[tile] = 0;        // every unit of the tile has counted
+        }
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        const Acc* part = reinterpret_cast<const Acc*>(g.scratch) + (size_t)ts.x * (TH * TW);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) acc[r] = __ldcg(part + r * NT + threadIdx.x);
+        for (int sl = 1; sl < ts.y; ++sl) {
 #pragma unroll
             for (int r = 0; r < RPT; ++r) {
-                if (wgt[k][r] != 0.f) {
-                    if constexpr (MODE == 0) {
-                        acc[r] += (double)wgt[k][r];
-                    } else {
-                        acc[r].x = fmaf(wgt[k][r], val[k][r].x, acc[r].x);
-                        acc[r].y = fmaf(wgt[k][r], val[k][r].y, acc[r].y);
-                    }
+                const Acc v = __ldcg(part + (size_t)sl * (TH * TW) + r * NT + threadIdx.x);
+                if constexpr (MODE == 0) {
+                    acc[r] += v;
+                } else {
+                    acc[r].x += v.x;
+                    acc[r].y += v.y;
                 }
             }
         }
@@ -104,7 +158,7 @@ __global__ void __launch_bounds__(gather_threads(TH)) gather_kernel(const __grid
     gather_body<MODE, TH>(g, blockIdx.x);
 }
 
-// Several jobs' tiles in one launch: CTA k gathers tile work[k].y of job work[k].x.
+// Several jobs' units in one launch: CTA k gathers unit work[k].y of job work[k].x.
 template <int MODE, int TH>
 __global__ void __launch_bounds__(gather_threads(TH))
 gather_kernel_batched(const GatherArgs* __restrict__ descs, const int2* __restrict__ work) {
@@ -113,12 +167,12 @@ gather_kernel_batched(const GatherArgs* __restrict__ descs, const int2* __restri
 }
 
 template <int MODE>
-static cudaError_t launch_gather(const GatherArgs& g, int ntiles, int tile_h, cudaStream_t s) {
-    if (ntiles <= 0) return cudaSuccess;
+static cudaError_t launch_gather(const GatherArgs& g, int nunits, int tile_h, cudaStream_t s) {
+    if (nunits <= 0) return cudaSuccess;
     switch (tile_h) {
-        case 8: gather_kernel<MODE, 8><<<ntiles, gather_threads(8), 0, s>>>(g); break;
-        case 16: gather_kernel<MODE, 16><<<ntiles, gather_threads(16), 0, s>>>(g); break;
-        case 32: gather_kernel<MODE, 32><<<ntiles, gather_threads(32), 0, s>>>(g); break;
+        case 8: gather_kernel<MODE, 8><<<nunits, gather_threads(8), 0, s>>>(g); break;
+        case 16: gather_kernel<MODE, 16><<<nunits, gather_threads(16), 0, s>>>(g); break;
+        case 32: gather_kernel<MODE, 32><<<nunits, gather_threads(32), 0, s>>>(g); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -127,13 +181,13 @@ cudaError_t launch_gather_weights(const GatherArgs& g, int n, int th, cudaStream
 cudaError_t launch_gather_consensus(const GatherArgs& g, int n, int th, cudaStream_t s) { return launch_gather<1>(g, n, th, s); }
 cudaError_t launch_gather_readout(const GatherArgs& g, int n, int th, cudaStream_t s) { return launch_gather<2>(g, n, th, s); }
 
-cudaError_t launch_gather_consensus_batched(const GatherArgs* descs, const int2* work, int ntiles, int tile_h,
+cudaError_t launch_gather_consensus_batched(const GatherArgs* descs, const int2* work, int nunits, int tile_h,
                                             cudaStream_t s) {
-    if (ntiles <= 0) return cudaSuccess;
+    if (nunits <= 0) return cudaSuccess;
     switch (tile_h) {
-        case 8: gather_kernel_batched<1, 8><<<ntiles, gather_threads(8), 0, s>>>(descs, work); break;
-        case 16: gather_kernel_batched<1, 16><<<ntiles, gather_threads(16), 0, s>>>(descs, work); break;
-        case 32: gather_kernel_batched<1, 32><<<ntiles, gather_threads(32), 0, s>>>(descs, work); break;
+        case 8: gather_kernel_batched<1, 8><<<nunits, gather_threads(8), 0, s>>>(descs, work); break;
+        case 16: gather_kernel_batched<1, 16><<<nunits, gather_threads(16), 0, s>>>(descs, work); break;
+        case 32: gather_kernel_batched<1, 32><<<nunits, gather_threads(32), 0, s>>>(descs, work); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

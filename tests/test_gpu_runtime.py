@@ -45,6 +45,22 @@ def test_graph_replay_is_bit_identical_to_direct_launches(cfg):
     b.close()
 
 
+@pytest.mark.parametrize("cfg", ["small", "p256"])
+def test_results_do_not_depend_on_the_gather_tile_height(cfg):
+    """Long tile lists are split over several CTAs at fixed window-index
+    blocks, so every pixel's sum order is the same for every tile height."""
+    w = datagen.make_workload(cfg, seed=45)
+    out = []
+    for th in (8, 16, 32):
+        rec = _job(w)
+        rec.set_plan(rec.plan()["variant"], th)
+        rec.iterate(5, 0.5, 0.5)
+        out.append((rec.image().cpu().numpy(), rec.patches().cpu().numpy(), rec.residual()))
+        rec.close()
+    for img, v, r in out[1:]:
+        assert np.array_equal(img, out[0][0]) and np.array_equal(v, out[0][1]) and r == out[0][2]
+
+
 def test_set_plan_midrun_matches_oracle():
     """Switching variants (and so the stored amplitude row order) mid-run
     keeps every later iteration within the parity bound."""
