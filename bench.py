@@ -42,7 +42,7 @@ WORKLOAD = ("p256: object 600x600 complex64, probe 256x256 (Gaussian sigma 48 px
             "Poisson peak 1e5, alpha 0.5, rho 0.5, kappa 1.25")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "agent_p256_traffic.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2111_14240_gb300", "csrc", f)
-                  for f in ("agent.cuh", "fft_smem.cuh", "pmace_internal.h")]
+                  for f in ("agent.cuh", "agent_xpose.cuh", "fft_smem.cuh", "pmace_internal.h")]
 
 
 def kernel_hash() -> str:
@@ -165,6 +165,11 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def agent_kernel_name(plan) -> str:
+    """The agent sweep kernel a plan launches (transposing exchange or in-place cross-CTA stage)."""
+    return "agent_xpose_kernel" if plan.get("exchange") else "agent_kernel"
 
 
 def stored_traffic():
@@ -317,7 +322,7 @@ def run_ours(args):
                    "l2": "no flush: per-step working set (q, u, y) is "
                          f"{(J * np_ * np_ * 20) / 1e6:.0f} MB > 129 MB L2",
                    "plan": plan},
-        "roofline": {"bound": "hbm", "kernel": "agent_kernel", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": agent_kernel_name(plan), "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": stored_traffic(),
                      "peak_kind": f"{peak_kind} (copy bandwidth)",
                      "algorithmic_bytes_per_launch": bytes_launch,

@@ -148,11 +148,16 @@ pmace_status pmace_kernel_times(pmace_handle h, double* agent_ms, int64_t* agent
 /* Kernel plan of this job: for the agent kernel the variant index, its
  * cluster size (CTAs per window), threads per CTA, dynamic shared memory per
  * CTA, columns per thread of the column step, whether the amplitudes are
- * staged in shared memory, and how many clusters the device holds at once;
- * for the consensus gather the image tile shape. */
+ * staged in shared memory, how many clusters the device holds at once, how
+ * the 2-D DFT is split over the cluster (exchange 0: an in-place cross-CTA
+ * butterfly stage; 1: a transposing exchange of 16 x 16 blocks between the
+ * Np / 16 CTAs, which then run their column transforms locally) and the
+ * windows each cluster processes; for the consensus gather the image tile
+ * shape. */
 typedef struct {
     int32_t cluster, threads, smem_bytes, tile_h, tile_w;
     int32_t variant, cols_per_thread, stage_y, max_clusters;
+    int32_t exchange, windows_per_cluster;
 } pmace_plan;
 pmace_status pmace_get_plan(pmace_handle h, pmace_plan* plan);
 

@@ -76,6 +76,54 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// S3 for one spectrum coefficient A (unnormalised 2-D DFT): y A / |A|, 0
+// where A = 0; coefficients whose squared magnitude would underflow are
+// rescaled by 2^100 first.  Adds (y - |A|/Np)^2 and y^2 to the residual sums.
+__device__ __forceinline__ float2 replace_magnitude(float2 xa, float y, float inv_n, float& acc_d, float& acc_y) {
+    float m2 = fmaf(xa.x, xa.x, xa.y * xa.y);
+    float unscale = inv_n;
+    if (m2 < 0x1p-100f) {
+        xa = xa * 0x1p100f;
+        m2 = fmaf(xa.x, xa.x, xa.y * xa.y);
+        unscale = inv_n * 0x1p-100f;
+    }
+    float2 o = make_float2(0.f, 0.f);
+    float mag = 0.f;
+    if (m2 > 0.f) {
+        const float rs = rsqrtf(m2);
+        mag = m2 * rs * unscale;
+        o = xa * (y * rs);
+    }
+    const float e = y - mag;
+    acc_d = fmaf(e, e, acc_d);
+    acc_y = fmaf(y, y, acc_y);
+    return o;
+}
+
+// S4 + S5 for one pixel: g = F^* A' unnormalised, q and xv the pending
+// stack and consensus values, dv = 1/d ((0, 0) where d is treated as
+// absent).  v = q + 2 rho_prev xv; w = (alpha v + D^-1 g / Np) / (1 + alpha)
+// (w = v where d is absent); u = 2w - v; q' = v - 2 rho w.  Adds |z - w|^2
+// (z = v on the first iteration, else xv) and |w|^2 to the residual sums.
+__device__ __forceinline__ void agent_update(float2 g, float2 q, float2 xv, float2 dv, float two_rho_prev, float scale,
+                                             float alpha, float inv1pa, float two_rho, bool first, float2& u, float2& qn,
+                                             float& az, float& aw) {
+    const float2 v = make_float2(fmaf(two_rho_prev, xv.x, q.x), fmaf(two_rho_prev, xv.y, q.y));
+    float2 w;
+    if (dv.x == 0.f && dv.y == 0.f) {
+        w = v;                                    // d treated as absent here
+    } else {
+        const float2 h = cmul(dv, g * scale);     // D^-1 F^* A'
+        w = make_float2(fmaf(alpha, v.x, h.x) * inv1pa, fmaf(alpha, v.y, h.y) * inv1pa);
+    }
+    u = make_float2(2.f * w.x - v.x, 2.f * w.y - v.y);
+    qn = make_float2(fmaf(-two_rho, w.x, v.x), fmaf(-two_rho, w.y, v.y));
+    const float2 z = first ? v : xv;
+    const float dzx = z.x - w.x, dzy = z.y - w.y;
+    az = fmaf(dzx, dzx, fmaf(dzy, dzy, az));
+    aw = fmaf(w.x, w.x, fmaf(w.y, w.y, aw));
+}
+
 // Per-CTA sums of four FP32 per-thread partials: warp sums in FP32 (32
 // terms), the warp totals added in FP64 in warp order by one thread.
 template <int T>
@@ -280,29 +328,7 @@ __device__ __forceinline__ void agent_body(const AgentArgs& a, const int j0) {
             Dft<R, false>::run(x);
             const float inv_n = 1.0f / (float)N;
 #pragma unroll
-            for (int k = 0; k < R; ++k) {
-                // phase A/|A| (0 only where A = 0); coefficients whose squared
-                // magnitude would underflow are rescaled by 2^100 first
-                float2 xa = x[k];
-                float m2 = fmaf(xa.x, xa.x, xa.y * xa.y);
-                float unscale = inv_n;
-                if (m2 < 0x1p-100f) {
-                    xa = xa * 0x1p100f;
-                    m2 = fmaf(xa.x, xa.x, xa.y * xa.y);
-                    unscale = inv_n * 0x1p-100f;
-                }
-                float2 o = make_float2(0.f, 0.f);
-                float mag = 0.f;
-                if (m2 > 0.f) {
-                    const float rs = rsqrtf(m2);
-                    mag = m2 * rs * unscale;
-                    o = xa * (yv[k] * rs);
-                }
-                const float e = yv[k] - mag;
-                acc_d[p] = fmaf(e, e, acc_d[p]);
-                acc_y[p] = fmaf(yv[k], yv[k], acc_y[p]);
-                x[k] = o;
-            }
+            for (int k = 0; k < R; ++k) x[k] = replace_magnitude(x[k], yv[k], inv_n, acc_d[p], acc_y[p]);
             Dft<R, true>::run(x);
 #pragma unroll
             for (int k = 0; k < R; ++k) cp[k * RS] = x[k];
@@ -354,22 +380,6 @@ __device__ __forceinline__ void agent_body(const AgentArgs& a, const int j0) {
 #pragma unroll
         for (int p = 0; p < PPC; ++p) {
             float az = 0.f, aw = 0.f;
-            auto agent_update = [&](float2 g, float2 q, float2 xv, float2 dv, float2& u, float2& qn) {
-                const float2 v = make_float2(fmaf(two_rho_prev, xv.x, q.x), fmaf(two_rho_prev, xv.y, q.y));
-                float2 w;
-                if (dv.x == 0.f && dv.y == 0.f) {
-                    w = v;                                    // d treated as absent here
-                } else {
-                    const float2 h = cmul(dv, g * scale);     // D^-1 F^* A'
-                    w = make_float2(fmaf(alpha, v.x, h.x) * inv1pa, fmaf(alpha, v.y, h.y) * inv1pa);
-                }
-                u = make_float2(2.f * w.x - v.x, 2.f * w.y - v.y);
-                qn = make_float2(fmaf(-two_rho, w.x, v.x), fmaf(-two_rho, w.y, v.y));
-                const float2 z = first ? v : xv;
-                const float dzx = z.x - w.x, dzy = z.y - w.y;
-                az = fmaf(dzx, dzx, fmaf(dzy, dzy, az));
-                aw = fmaf(w.x, w.x, fmaf(w.y, w.y, aw));
-            };
             if (valid(p)) {
                 const int2 off = a.offs[j0 + p];
                 float2* qp = a.q + pbase_of(p);   // read (S0) and overwritten (S5) pair by pair by one thread
@@ -394,8 +404,10 @@ __device__ __forceinline__ void agent_body(const AgentArgs& a, const int j0) {
                         const int row = t / HALF, c = 2 * (t % HALF);
                         const float2* src = tp + row * RS + pcol(c);
                         float2 u0, u1, q0, q1;
-                        agent_update(src[0], make_float2(qv[i].x, qv[i].y), x0[i], make_float2(dv[i].x, dv[i].y), u0, q0);
-                        agent_update(src[1], make_float2(qv[i].z, qv[i].w), x1[i], make_float2(dv[i].z, dv[i].w), u1, q1);
+                        agent_update(src[0], make_float2(qv[i].x, qv[i].y), x0[i], make_float2(dv[i].x, dv[i].y),
+                                     two_rho_prev, scale, alpha, inv1pa, two_rho, first, u0, q0, az, aw);
+                        agent_update(src[1], make_float2(qv[i].z, qv[i].w), x1[i], make_float2(dv[i].z, dv[i].w),
+                                     two_rho_prev, scale, alpha, inv1pa, two_rho, first, u1, q1, az, aw);
                         *reinterpret_cast<float4*>(uo + row * N + c) = make_float4(u0.x, u0.y, u1.x, u1.y);
                         *reinterpret_cast<float4*>(qp + row * N + c) = make_float4(q0.x, q0.y, q1.x, q1.y);
                     }

@@ -1,0 +1,438 @@
+// The fused agent sweep (steps S0-S5 of one PMACE iteration, the same
+// arithmetic as agent.cuh) with the 2-D DFT split over a cluster by a
+// transposing exchange instead of an in-place cross-CTA stage.
+//
+// A window is Np x Np; its cluster has C = Np / 16 CTAs.  CTA `rank` holds
+// two 16 Np-element slabs in shared memory:
+//   A  window rows [16 rank, 16 rank + 16), all Np columns (row slab);
+//   B  all Np rows of storage columns [16 rank, 16 rank + 16) (column slab).
+// Both are stored as C blocks of 16 x 16 elements; block p of A holds
+// columns [16 p, 16 p + 16) of the CTA's rows, block r of B holds rows
+// [16 r, 16 r + 16) of the CTA's columns, and inside a block element
+// (k, c) sits at k * 16 + (c ^ k), which keeps every access pattern of the
+// radix stages free of bank conflicts.  Block p of A is exactly block
+// `rank` of CTA p's B, so one 2 KB bulk copy per peer moves the row slabs
+// into the column slabs, and one per peer moves them back.
+//
+// Per window:
+//   rows   copy-in fused with the first (span Np) DIF row stage, in
+//          registers; second row stage in A;
+//   A -> B bulk copies (cp.async.bulk shared::cta -> shared::cluster), each
+//          counted on the receiving CTA's mbarrier;
+//   cols   first DIF column stage in B; second column stage, magnitude
+//          replacement (S3) and the inverse second stage in registers;
+//          inverse first column stage in B;
+//   B -> A bulk copies back;
+//   rows   inverse second row stage in A; inverse first row stage fused
+//          with the agent update and the stores of u and q (S4, S5).
+//
+// No cluster-wide barrier is needed between windows: a CTA sends block p of
+// a slab only after it has received everything it needs from the previous
+// exchange, and every CTA receives a block into exactly the region whose
+// previous contents it has already sent on, so the mbarrier of the
+// receiving slab is the only synchronisation (see the ordering notes at
+// the sends).  A cluster processes a contiguous run of windows and
+// synchronises once at the start (barrier initialisation) and once at the
+// end (no CTA exits while a peer's copy may still target it).  Every wait
+// is bounded: a wait that gives up sets bit 2 of *err and the sweep runs on
+// (its results are then wrong, and the host reports PMACE_ERR_TIMEOUT).
+#pragma once
+
+#include "agent.cuh"
+
+namespace pmace {
+
+template <int N>
+struct XposeGeom {
+    static constexpr int R = 16;                    // rows (and columns) per CTA
+    static constexpr int C = N / R;                 // CTAs per window
+    static constexpr int kThreads = N;
+    static constexpr int kBlk = R * R;              // elements per exchange block
+    static constexpr int kSlab = C * kBlk;          // elements per slab (16 N)
+    static constexpr int kBlkBytes = kBlk * (int)sizeof(float2);
+    static constexpr RadixPlan kRad = radix_plan(N);
+    static constexpr int r1 = kRad.first, r2 = kRad.second;
+    static constexpr int S1 = N / r1;               // stride of the first stage (= r2)
+    static constexpr int NB1 = R * S1;              // first-stage butterflies per slab
+    static constexpr int NB2 = R * r1;              // second-stage butterflies per slab
+    static constexpr int kSmem = 2 * kSlab * (int)sizeof(float2) + N * (int)sizeof(float2) + 16;
+    // resident CTAs per SM: shared memory (228 KB, 1 KB reserved per CTA plus
+    // the static reduction buffer), threads, and at least 64 registers a thread
+    static constexpr int kBySmem = (228 * 1024) / (kSmem + 2048);
+    static constexpr int kByThreads = 2048 / kThreads;
+    static constexpr int kByRegs = 65536 / (kThreads * 64);
+    static constexpr int kMinBlocks0 = kBySmem < kByThreads ? kBySmem : kByThreads;
+    static constexpr int kMinBlocks = kMinBlocks0 < kByRegs ? kMinBlocks0 : kByRegs;
+    static_assert(r1 * r2 == N && r2 > 1, "two radix stages per axis");
+    static_assert(NB1 % kThreads == 0 && NB2 % kThreads == 0, "stages must split evenly over threads");
+    static_assert(C >= 2 && C <= 16, "one block per CTA of the cluster");
+};
+
+// Slab index of element (k, c) of block blk.
+__device__ __forceinline__ int xslab(int blk, int k, int c) { return blk * 256 + k * 16 + (c ^ k); }
+// Row slab: window row k of the CTA, storage column s.
+__device__ __forceinline__ int xrow(int k, int s) { return xslab(s >> 4, k, s & 15); }
+// Column slab: storage row g, column c of the CTA.
+__device__ __forceinline__ int xcol(int g, int c) { return xslab(g >> 4, g & 15, c); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Make this thread's generic-proxy shared-memory writes visible to the bulk
+// copies (async proxy) issued after the next barrier.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Copy `bytes` from this CTA's shared memory to shared memory of a CTA of
+// the cluster; completion is counted on that CTA's mbarrier `bar`.
+__device__ __forceinline__ void bulk_copy_to_peer(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "r"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Hint the L2 to fetch `bytes` (a multiple of 16) from global address p.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Polls of one wait before it gives up (try_wait may also suspend the
+// thread for a while on each poll).
+constexpr uint32_t kXposeSpinLimit = 1u << 22;
+
+__device__ __forceinline__ void mbar_wait_bounded(uint32_t bar, uint32_t parity, int* err) {
+    for (uint32_t it = 0; it < kXposeSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return;
+    if (err) atomicOr(err, 2);
+}
+
+// Windows j0 .. jn - 1 of the job `a` on one cluster.
+template <int N, int AMP>
+__device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, const int jn) {
+    using G = XposeGeom<N>;
+    constexpr int C = G::C, T = G::kThreads, r1 = G::r1, r2 = G::r2, S1 = G::S1;
+    constexpr int U2 = G::NB2 / T;   // second-stage butterflies per thread
+    constexpr uint32_t kBlkBytes = G::kBlkBytes, kBytes = C * G::kBlkBytes;
+
+    extern __shared__ float4 smem_raw[];
+    float2* sA = reinterpret_cast<float2*>(smem_raw);
+    float2* sB = sA + G::kSlab;
+    float2* tw = sB + G::kSlab;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tw + N);   // [0]: B slab filled, [1]: A slab filled
+    __shared__ double red[(T / 32) * 4];
+
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const uint32_t a_base = smem_addr(sA), b_base = smem_addr(sB);
+    const uint32_t bar_b = smem_addr(bars), bar_a = smem_addr(bars + 1);
+    if (threadIdx.x == 0) {
+        mbar_init(bar_b, 1);
+        mbar_init(bar_a, 1);
+        mbar_fence_init();
+        mbar_arrive_expect_tx(bar_b, kBytes);
+        mbar_arrive_expect_tx(bar_a, kBytes);
+    }
+    for (int i = threadIdx.x; i < N; i += T) tw[i] = a.tw[i];
+    cl.sync();   // every CTA's barriers are armed before any copy can land
+
+    const float two_rho_prev = 2.0f * a.rho_prev;
+    const float inv_n = 1.0f / (float)N;
+    const float scale = 1.0f / (float)N;            // orthonormal F^*
+    const float inv1pa = 1.0f / (1.0f + a.alpha);
+    const float alpha = a.alpha;
+    const float two_rho = 2.0f * a.rho_cur;
+    const bool first = a.first != 0;
+    const int row0 = rank * G::R;
+    uint32_t parity = 0;
+
+    // the CTA's stack rows and amplitude rows of a window (one thread each)
+    auto prefetch_window = [&](int jw) {
+        const size_t rb = ((size_t)jw * N + row0) * N;
+        if (threadIdx.x == 0) prefetch_l2(a.q + rb, G::R * N * (uint32_t)sizeof(float2));
+        else if (threadIdx.x == T - 1) prefetch_l2(static_cast<const char*>(a.y) + rb * (AMP ? 2 : 4), G::R * N * (AMP ? 2 : 4));
+    };
+    prefetch_window(j0);
+
+#pragma unroll 1
+    for (int j = j0; j < jn; ++j) {
+        const int2 off = a.offs[j];
+        const size_t wbase = (size_t)j * N * N;
+        float yscale = 1.0f;
+        if constexpr (AMP == 1) yscale = __ldg(a.yscale + j);
+        if (j + 1 < jn) prefetch_window(j + 1);   // while this window is in flight
+
+        // ---- S0 + S1 fused with the first DIF row stage (span N, radix r1)
+#pragma unroll 1
+        for (int id = threadIdx.x; id < G::NB1; id += T) {
+            const int k = id / S1, b = id % S1;
+            const int row = row0 + k;
+            const float2* qr = a.q + wbase + (size_t)row * N;
+            const float2* __restrict__ dr = a.probe + (size_t)row * N;
+            const float2* __restrict__ xr = a.xbar + (size_t)(off.x + row) * a.n2 + off.y;
+            // all stack loads first (one memory round trip), then the
+            // L2-resident consensus and probe values
+            float2 x[r1];
+#pragma unroll
+            for (int t = 0; t < r1; ++t) x[t] = qr[b + S1 * t];
+#pragma unroll
+            for (int t = 0; t < r1; ++t) {
+                const float2 xv = __ldg(xr + b + S1 * t);
+                x[t] = make_float2(fmaf(two_rho_prev, xv.x, x[t].x), fmaf(two_rho_prev, xv.y, x[t].y));
+            }
+#pragma unroll
+            for (int t = 0; t < r1; ++t) x[t] = cmul(__ldg(dr + b + S1 * t), x[t]);
+            Dft<r1, false>::run(x);
+#pragma unroll
+            for (int t = 1; t < r1; ++t) x[t] = cmul(x[t], tw[b * t]);
+#pragma unroll
+            for (int t = 0; t < r1; ++t) sA[xrow(k, b + S1 * t)] = x[t];
+        }
+        __syncthreads();
+        // ---- second DIF row stage (span r2)
+#pragma unroll 1
+        for (int id = threadIdx.x; id < G::NB2; id += T) {
+            const int k = id % 16, m = id / 16;
+            float2 x[r2];
+#pragma unroll
+            for (int i = 0; i < r2; ++i) x[i] = sA[xrow(k, m * r2 + i)];
+            Dft<r2, false>::run(x);
+#pragma unroll
+            for (int i = 0; i < r2; ++i) sA[xrow(k, m * r2 + i)] = x[i];
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        // ---- A -> B.  Block `rank` of peer p's B was last read by p's own
+        // copy of it back to this CTA in the previous window, which landed
+        // before this CTA passed its wait on the A slab: p's region is free.
+        if (threadIdx.x < C) {
+            const uint32_t p = threadIdx.x;
+            bulk_copy_to_peer(cluster_addr(b_base + (uint32_t)rank * kBlkBytes, p), a_base + p * kBlkBytes, kBlkBytes,
+                              cluster_addr(bar_b, p));
+        }
+        // amplitudes of this thread's column butterflies, loaded while the exchange is in flight
+        float yv[U2][r2];
+#pragma unroll
+        for (int u = 0; u < U2; ++u) {
+            const int id = threadIdx.x + u * T;
+            const int c = id % 16, m = id / 16;
+#pragma unroll
+            for (int i = 0; i < r2; ++i) yv[u][i] = load_amp<AMP>(a.y, wbase + (size_t)(m * r2 + i) * N + row0 + c, yscale);
+        }
+        mbar_wait_bounded(bar_b, parity, a.err);
+        // re-arm for the next window before this CTA's next send: every
+        // peer's next A -> B copy comes after it has received that send
+        if (threadIdx.x == 0 && j + 1 < jn) mbar_arrive_expect_tx(bar_b, kBytes);
+
+        // ---- first DIF column stage (span N, radix r1)
+#pragma unroll 1
+        for (int id = threadIdx.x; id < G::NB1; id += T) {
+            const int c = id % 16, b = id / 16;
+            float2 x[r1];
+#pragma unroll
+            for (int t = 0; t < r1; ++t) x[t] = sB[xcol(b + S1 * t, c)];
+            Dft<r1, false>::run(x);
+#pragma unroll
+            for (int t = 1; t < r1; ++t) x[t] = cmul(x[t], tw[b * t]);
+#pragma unroll
+            for (int t = 0; t < r1; ++t) sB[xcol(b + S1 * t, c)] = x[t];
+        }
+        __syncthreads();
+        // ---- second column stage, S3, inverse second column stage
+        float acc_d = 0.f, acc_y = 0.f;
+#pragma unroll
+        for (int u = 0; u < U2; ++u) {
+            const int id = threadIdx.x + u * T;
+            const int c = id % 16, m = id / 16;
+            float2 x[r2];
+#pragma unroll
+            for (int i = 0; i < r2; ++i) x[i] = sB[xcol(m * r2 + i, c)];
+            Dft<r2, false>::run(x);
+#pragma unroll
+            for (int i = 0; i < r2; ++i) x[i] = replace_magnitude(x[i], yv[u][i], inv_n, acc_d, acc_y);
+            Dft<r2, true>::run(x);
+#pragma unroll
+            for (int i = 0; i < r2; ++i) sB[xcol(m * r2 + i, c)] = x[i];
+        }
+        __syncthreads();
+        // ---- inverse first column stage (DIT, span N)
+#pragma unroll 1
+        for (int id = threadIdx.x; id < G::NB1; id += T) {
+            const int c = id % 16, b = id / 16;
+            float2 x[r1];
+#pragma unroll
+            for (int t = 0; t < r1; ++t) x[t] = sB[xcol(b + S1 * t, c)];
+#pragma unroll
+            for (int t = 1; t < r1; ++t) x[t] = cmulc(x[t], tw[b * t]);
+            Dft<r1, true>::run(x);
+#pragma unroll
+            for (int t = 0; t < r1; ++t) sB[xcol(b + S1 * t, c)] = x[t];
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        // ---- B -> A.  Block `rank` of peer p's A is the block p sent here
+        // in this window, which has landed (this CTA passed its wait on B).
+        if (threadIdx.x < C) {
+            const uint32_t p = threadIdx.x;
+            bulk_copy_to_peer(cluster_addr(a_base + (uint32_t)rank * kBlkBytes, p), b_base + p * kBlkBytes, kBlkBytes,
+                              cluster_addr(bar_a, p));
+        }
+        mbar_wait_bounded(bar_a, parity, a.err);
+        if (threadIdx.x == 0 && j + 1 < jn) mbar_arrive_expect_tx(bar_a, kBytes);
+
+        // ---- inverse second row stage (span r2)
+#pragma unroll 1
+        for (int id = threadIdx.x; id < G::NB2; id += T) {
+            const int k = id % 16, m = id / 16;
+            float2 x[r2];
+#pragma unroll
+            for (int i = 0; i < r2; ++i) x[i] = sA[xrow(k, m * r2 + i)];
+            Dft<r2, true>::run(x);
+#pragma unroll
+            for (int i = 0; i < r2; ++i) sA[xrow(k, m * r2 + i)] = x[i];
+        }
+        __syncthreads();
+        // ---- inverse first row stage fused with S4 + S5
+        float acc_z = 0.f, acc_w = 0.f;
+#pragma unroll 1
+        for (int id = threadIdx.x; id < G::NB1; id += T) {
+            const int k = id / S1, b = id % S1;
+            const int row = row0 + k;
+            float2 x[r1];
+#pragma unroll
+            for (int t = 0; t < r1; ++t) x[t] = sA[xrow(k, b + S1 * t)];
+#pragma unroll
+            for (int t = 1; t < r1; ++t) x[t] = cmulc(x[t], tw[b * t]);
+            Dft<r1, true>::run(x);
+            float2* qr = a.q + wbase + (size_t)row * N;   // read (S0) and overwritten (S5) by this thread only
+            float2* __restrict__ ur = a.u + wbase + (size_t)row * N;
+            const float2* __restrict__ dr = a.dinv + (size_t)row * N;
+            const float2* __restrict__ xr = a.xbar + (size_t)(off.x + row) * a.n2 + off.y;
+            // in quarters: the loads of a quarter are issued together
+            constexpr int H = r1 / 4;
+#pragma unroll
+            for (int h0 = 0; h0 < r1; h0 += H) {
+                float2 qv[H], xv[H], dv[H];
+#pragma unroll
+                for (int t = 0; t < H; ++t) {
+                    const int s = b + S1 * (h0 + t);
+                    qv[t] = qr[s];
+                    xv[t] = __ldg(xr + s);
+                    dv[t] = __ldg(dr + s);
+                }
+#pragma unroll
+                for (int t = 0; t < H; ++t) {
+                    const int s = b + S1 * (h0 + t);
+                    float2 u, qn;
+                    agent_update(x[h0 + t], qv[t], xv[t], dv[t], two_rho_prev, scale, alpha, inv1pa, two_rho, first,
+                                 u, qn, acc_z, acc_w);
+                    ur[s] = u;
+                    qr[s] = qn;
+                }
+            }
+        }
+        float acc[4] = {acc_z, acc_w, acc_d, acc_y};
+        block_reduce4<T>(acc, red, a.partials + ((size_t)j * C + rank) * 4);
+        parity ^= 1u;
+    }
+    cl.sync();   // every copy into this CTA has landed; no peer still reads from it
+}
+
+// One job: cluster k processes windows [k wpc, min((k + 1) wpc, J)).
+template <int N, int AMP>
+__global__ void __launch_bounds__(XposeGeom<N>::kThreads, XposeGeom<N>::kMinBlocks)
+agent_xpose_kernel(const __grid_constant__ AgentArgs a) {
+    const int j0 = (int)(blockIdx.x / XposeGeom<N>::C) * a.wpc;
+    xpose_body<N, AMP>(a, j0, min(j0 + a.wpc, a.J));
+}
+
+// Several jobs: cluster k processes job work[k].x from window work[k].y on,
+// that job's wpc windows at most.
+template <int N, int AMP>
+__global__ void __launch_bounds__(XposeGeom<N>::kThreads, XposeGeom<N>::kMinBlocks)
+agent_xpose_kernel_batched(const AgentArgs* __restrict__ descs, const int2* __restrict__ work) {
+    const int2 w = work[blockIdx.x / XposeGeom<N>::C];
+    const AgentArgs& a = descs[w.x];
+    xpose_body<N, AMP>(a, w.y, min(w.y + a.wpc, a.J));
+}
+
+template <int N, typename K>
+cudaLaunchConfig_t xpose_config(K, int nclusters, cudaStream_t s, cudaLaunchAttribute* attr) {
+    using G = XposeGeom<N>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nclusters * G::C), 1, 1);
+    cfg.blockDim = dim3(G::kThreads, 1, 1);
+    cfg.dynamicSmemBytes = G::kSmem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = G::C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+template <typename K>
+cudaError_t xpose_attributes(K fn, int smem, int cluster) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess && cluster > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+// Query (a == nullptr: fills info, max_clusters from the occupancy API) or
+// launch ceil(J / a->wpc) clusters.
+template <int N>
+cudaError_t agent_xpose(const AgentArgs* a, int amp_f16, cudaStream_t s, AgentPlanInfo* info) {
+    using G = XposeGeom<N>;
+    void (*fn)(const AgentArgs) = amp_f16 ? agent_xpose_kernel<N, 1> : agent_xpose_kernel<N, 0>;
+    cudaError_t e = xpose_attributes(fn, G::kSmem, G::C);
+    if (a == nullptr) {
+        info->threads = G::kThreads;
+        info->smem_bytes = G::kSmem;
+        info->max_clusters = 0;
+        if (e == cudaSuccess) {
+            cudaLaunchAttribute attr[1];
+            cudaLaunchConfig_t cfg = xpose_config<N>(fn, 64, nullptr, attr);
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess) info->max_clusters = n;
+        }
+        cudaGetLastError();
+        info->launchable = info->max_clusters > 0;
+        return cudaSuccess;
+    }
+    if (e != cudaSuccess) return e;
+    if (a->wpc <= 0) return cudaErrorInvalidValue;
+    const int nclusters = (a->J + a->wpc - 1) / a->wpc;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = xpose_config<N>(fn, nclusters, s, attr);
+    return cudaLaunchKernelEx(&cfg, fn, *a);
+}
+
+template <int N>
+cudaError_t agent_xpose_batched(const AgentArgs* descs, const int2* work, int nclusters, int amp_f16,
+                                cudaStream_t s) {
+    using G = XposeGeom<N>;
+    if (nclusters <= 0) return cudaSuccess;
+    void (*fn)(const AgentArgs*, const int2*) =
+        amp_f16 ? agent_xpose_kernel_batched<N, 1> : agent_xpose_kernel_batched<N, 0>;
+    cudaError_t e = xpose_attributes(fn, G::kSmem, G::C);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = xpose_config<N>(fn, nclusters, s, attr);
+    return cudaLaunchKernelEx(&cfg, fn, descs, work);
+}
+
+}  // namespace pmace

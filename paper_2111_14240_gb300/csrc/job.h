@@ -24,6 +24,7 @@ struct pmace_job {
     int amp_f16 = 0;
     int cluster = 1;
     int variant = 0;
+    int wpc = 1;              // windows per agent cluster
     pmace::AgentPlanInfo plan{};
     int tiles_x = 0, tiles_y = 0, ntiles = 0;
     int tile_h = 16;          // gather tile height (rows), width kGatherTileW

@@ -87,7 +87,8 @@ cudaError_t agent_entry(int np, const AgentArgs* a, int variant, int amp, cudaSt
 
 // Agent variant to start from: PMACE_AGENT_PLAN (an index into
 // agent_variant_of) when set and valid, else PMACE_AGENT_CLUSTER selects the
-// first variant with that cluster size, else variant 0.
+// first variant with that cluster size, else the probe size's default
+// (default_agent_variant).
 int default_variant(int np) {
     if (const char* env = std::getenv("PMACE_AGENT_PLAN")) {
         const int v = std::atoi(env);
@@ -98,7 +99,7 @@ int default_variant(int np) {
         for (int v = 0; v < kAgentVariants; ++v)
             if (agent_variant_of(np, v).cluster == c) return v;
     }
-    return 0;
+    return default_agent_variant(np);
 }
 
 // Row order of the amplitudes for a cluster size: kernel row g holds
@@ -131,6 +132,32 @@ std::vector<int> radices_of(int L) {
     std::vector<int> v{p.first};
     if (p.second > 1) v.push_back(p.second);
     return v;
+}
+
+// Row order of the amplitudes for an agent variant: the in-place cross-CTA
+// variants leave the column axis in column_order; the transposing exchange
+// runs the same two DIF stages along columns as along rows, so both axes end
+// in the DIF order.
+std::vector<int> amp_row_order(int np, int variant) {
+    const AgentVariant v = agent_variant_of(np, variant);
+    if (!v.exchange) return column_order(np, v.cluster);
+    std::vector<int> perm;
+    dif_order(radices_of(np), 0, np, perm);
+    return perm;
+}
+
+// Windows each agent cluster processes: the variant's own count, or for the
+// transposing exchange (a run of windows per cluster) J spread evenly over
+// the clusters the device holds at once (PMACE_AGENT_WPC fixes the run).
+int windows_per_cluster(int np, int variant, int J, const AgentPlanInfo& info) {
+    const AgentVariant v = agent_variant_of(np, variant);
+    if (!v.exchange) return v.windows;
+    if (const char* env = std::getenv("PMACE_AGENT_WPC")) {   // fixed run length
+        const int w = std::atoi(env);
+        if (w > 0) return w;
+    }
+    const int m = std::max(info.max_clusters, 1);
+    return std::max(1, (J + m - 1) / m);
 }
 
 // Gather tables of one tile height: for every tile_h x kGatherTileW image
@@ -341,7 +368,7 @@ pmace_status build_tables(pmace_job* h, const std::vector<float>& probe_h,
     // row stages leave each row digit-reversed; along columns, local row k2
     // of CTA `rank` holds frequency rank + cluster * k2 after the cross-CTA
     // stage and the in-register column DFT
-    std::vector<int> rowperm, colperm = column_order(np, h->cluster);
+    std::vector<int> rowperm, colperm = amp_row_order(np, h->variant);
     dif_order(radices_of(np), 0, np, rowperm);
 
     PM_CUDA(h, dalloc(h, &h->probe, P));
@@ -443,6 +470,8 @@ AgentArgs agent_args(const pmace_job* h, float alpha, float rho) {
     a.rho_cur = rho;
     a.rho_prev = h->rho_pending;
     a.first = h->iterations == 0 ? 1 : 0;
+    a.wpc = h->wpc;
+    a.err = h->err;
     return a;
 }
 }  // namespace pmace
@@ -521,8 +550,8 @@ pmace_status switch_plan(pmace_job* h, int variant, int tile_h, cudaStream_t s) 
             return fail(h, PMACE_ERR_UNSUPPORTED_SIZE, "agent variant %d cannot run on this device", variant);
         }
         const int c_new = agent_variant_of(np, variant).cluster;
-        if (c_new != h->cluster) {
-            const std::vector<int> o_old = column_order(np, h->cluster), o_new = column_order(np, c_new);
+        const std::vector<int> o_old = amp_row_order(np, h->variant), o_new = amp_row_order(np, variant);
+        if (o_old != o_new) {
             std::vector<int> inv(np), map(np);
             for (int g = 0; g < np; ++g) inv[o_old[g]] = g;
             for (int g = 0; g < np; ++g) map[g] = inv[o_new[g]];   // new row g <- old row map[g]
@@ -539,6 +568,7 @@ pmace_status switch_plan(pmace_job* h, int variant, int tile_h, cudaStream_t s) 
         h->variant = variant;
         h->cluster = c_new;
         h->plan = info;
+        h->wpc = windows_per_cluster(np, variant, J, info);
     }
     if (tile_h != h->tile_h) {
         const pmace_status st = install_gather_tables(h, tile_h, s);
@@ -639,6 +669,7 @@ pmace_status pmace_create(const pmace_dims* dims, const float* probe, const int3
             return bail(fail(h, PMACE_ERR_UNSUPPORTED_SIZE, "no launchable agent plan for np=%d", np));
         h->variant = chosen;
         h->cluster = agent_variant_of(np, chosen).cluster;
+        h->wpc = windows_per_cluster(np, chosen, J, h->plan);
     }
     // gather tile height: PMACE_GATHER_TILE_H in {8, 16, 32}, default 16
     if (const char* env = std::getenv("PMACE_GATHER_TILE_H")) {
@@ -915,9 +946,12 @@ pmace_status pmace_residual(pmace_handle h, double out[2], void* stream) {
     if (h->iterations == 0) return fail(h, PMACE_ERR_STATE, "no iteration has run yet");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double r[4] = {0, 0, 0, 0};
+    int errflag = 0;
     PM_CUDA(h, launch_reduce_partials(h->partials, h->dims.J * h->cluster, 4, h->red_out, s));
     PM_CUDA(h, cudaMemcpyAsync(r, h->red_out, sizeof(r), cudaMemcpyDeviceToHost, s));
+    PM_CUDA(h, cudaMemcpyAsync(&errflag, h->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     PM_CUDA(h, cudaStreamSynchronize(s));
+    if (errflag & 2) return fail(h, PMACE_ERR_TIMEOUT, "a bounded wait of the agent sweep's exchange gave up");
     out[0] = r[1] > 0 ? std::sqrt(r[0] / r[1]) : 0.0;
     out[1] = r[3] > 0 ? r[2] / r[3] : 0.0;
     return PMACE_OK;
@@ -1000,6 +1034,8 @@ pmace_status pmace_get_plan(pmace_handle h, pmace_plan* plan) {
     plan->cols_per_thread = v.cols_per_thread;
     plan->stage_y = v.stage_y;
     plan->max_clusters = h->plan.max_clusters;
+    plan->exchange = v.exchange;
+    plan->windows_per_cluster = h->wpc;
     return PMACE_OK;
 }
 

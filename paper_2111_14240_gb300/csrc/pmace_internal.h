@@ -38,6 +38,8 @@ struct AgentArgs {
     int J;
     float alpha, rho_prev, rho_cur;
     int first;              // 1 on the first iteration of the job
+    int wpc;                // windows per cluster (transposing-exchange variant)
+    int* err;               // bit 2 set when a bounded device-side wait gives up
 };
 
 // Arguments of the pixel-owner gathers (weight image, consensus, readout).
@@ -78,19 +80,31 @@ __host__ __device__ constexpr int gather_threads(int tile_h) {
 
 // Agent kernel variants compiled for each probe size: CTAs per window,
 // columns per thread in the column step, amplitude staging in shared memory,
-// windows per cluster.
-// Index 0 is the default; pmace_autotune and PMACE_AGENT_PLAN pick others.
+// windows per cluster, and how the 2-D DFT is split over the cluster
+// (exchange 0: an in-place cross-CTA butterfly stage through distributed
+// shared memory, agent.cuh; 1: a transposing exchange of 16 x 16 blocks by
+// bulk copies, Np / 16 CTAs, a run of windows per cluster, agent_xpose.cuh).
+// default_agent_variant is where a job starts; pmace_autotune and
+// PMACE_AGENT_PLAN pick others.
 struct AgentVariant {
-    int cluster, cols_per_thread, stage_y, windows;
+    int cluster, cols_per_thread, stage_y, windows, exchange;
 };
-constexpr int kAgentVariants = 4;
+constexpr int kAgentVariants = 5;
 __host__ __device__ constexpr AgentVariant agent_variant_of(int np, int v) {
-    constexpr AgentVariant t32[kAgentVariants] = {{2, 1, 1, 1}, {1, 1, 1, 1}, {2, 1, 0, 2}, {1, 1, 0, 1}};
-    constexpr AgentVariant t64[kAgentVariants] = {{4, 1, 1, 1}, {4, 2, 0, 1}, {2, 1, 1, 1}, {4, 1, 0, 2}};
-    constexpr AgentVariant t128[kAgentVariants] = {{8, 2, 0, 1}, {8, 1, 1, 1}, {4, 1, 1, 1}, {8, 2, 0, 2}};
-    constexpr AgentVariant t256[kAgentVariants] = {{16, 2, 0, 1}, {16, 2, 0, 2}, {8, 1, 1, 1}, {8, 2, 0, 1}};
+    constexpr AgentVariant t32[kAgentVariants] = {
+        {2, 1, 1, 1, 0}, {1, 1, 1, 1, 0}, {2, 1, 0, 2, 0}, {1, 1, 0, 1, 0}, {2, 1, 0, 1, 1}};
+    constexpr AgentVariant t64[kAgentVariants] = {
+        {4, 1, 1, 1, 0}, {4, 2, 0, 1, 0}, {2, 1, 1, 1, 0}, {4, 1, 0, 2, 0}, {4, 1, 0, 1, 1}};
+    constexpr AgentVariant t128[kAgentVariants] = {
+        {8, 2, 0, 1, 0}, {8, 1, 1, 1, 0}, {4, 1, 1, 1, 0}, {8, 2, 0, 2, 0}, {8, 1, 0, 1, 1}};
+    constexpr AgentVariant t256[kAgentVariants] = {
+        {16, 2, 0, 1, 0}, {16, 2, 0, 2, 0}, {8, 1, 1, 1, 0}, {8, 2, 0, 1, 0}, {16, 1, 0, 1, 1}};
     return np == 32 ? t32[v] : np == 64 ? t64[v] : np == 128 ? t128[v] : t256[v];
 }
+// The fastest variant measured on GB300 for each probe size: the in-place
+// cross-CTA stage for 32 x 32 and 64 x 64 probes, the transposing exchange
+// (variant 4) for 128 x 128 and 256 x 256.
+__host__ __device__ constexpr int default_agent_variant(int np) { return np >= 128 ? 4 : 0; }
 
 // Geometry of one agent plan (probe size, CTAs per patch).
 struct AgentPlanInfo {

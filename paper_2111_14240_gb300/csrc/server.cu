@@ -280,12 +280,11 @@ pmace_status pmace_server::tick() {
     std::vector<int> stepping;
     for (auto& g : groups) {
         Launch L{std::get<0>(g.first), std::get<1>(g.first), std::get<2>(g.first), (int)awork.size(), 0};
-        const int ppc = agent_variant_of(L.np, L.variant).windows;
         for (int i : g.second) {
             const Active& a = active[i];
             const int jd = (int)adesc.size();
             adesc.push_back(agent_args(a.job, a.req.step.alpha, a.req.step.rho));
-            for (int j0 = 0; j0 < a.job->dims.J; j0 += ppc) awork.push_back(make_int2(jd, j0));
+            for (int j0 = 0; j0 < a.job->dims.J; j0 += a.job->wpc) awork.push_back(make_int2(jd, j0));
             stepping.push_back(i);
         }
         L.nclusters = (int)awork.size() - L.first_cluster;

@@ -46,7 +46,8 @@ class pmace_plan(ctypes.Structure):
                 ("smem_bytes", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("tile_w", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("cols_per_thread", ctypes.c_int32), ("stage_y", ctypes.c_int32),
-                ("max_clusters", ctypes.c_int32)]
+                ("max_clusters", ctypes.c_int32), ("exchange", ctypes.c_int32),
+                ("windows_per_cluster", ctypes.c_int32)]
 
 
 class pmace_server_config(ctypes.Structure):

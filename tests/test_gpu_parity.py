@@ -57,7 +57,7 @@ def test_five_iterations_small():
     assert abs(g["r_data"] - o["r_data"]) < 1e-4 * o["r_data"]
 
 
-VARIANTS = [0, 1, 2, 3]   # every compiled agent kernel variant of a probe size
+VARIANTS = [0, 1, 2, 3, 4]   # every compiled agent kernel variant of a probe size
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -89,6 +89,19 @@ def test_one_iteration_np256_full_config(variant):
     assert g["plan"]["variant"] == variant
 
 
+@pytest.mark.parametrize("cfg,wpc", [("small", 4), ("mid64", 5), ("mid128", 7)])
+def test_exchange_variant_runs_of_windows(cfg, wpc, monkeypatch):
+    """The transposing-exchange variant with a fixed run of windows per
+    cluster (the last run shorter), three iterations: the per-slab barriers
+    are re-armed window after window and iteration after iteration."""
+    spec = {"small": "small", "mid64": dict(MID64, name="mid64"), "mid128": dict(MID128, name="mid128")}[cfg]
+    w = datagen.make_workload(spec, seed=31)
+    assert w.J % wpc != 0
+    monkeypatch.setenv("PMACE_AGENT_WPC", str(wpc))
+    g, _ = _check_iteration(w, 3, variant=4)
+    assert g["plan"]["exchange"] == 1 and g["plan"]["windows_per_cluster"] == wpc
+
+
 def _midrun_step(w, k, alpha=0.5, rho=0.5, variant=None):
     """One iteration from the FP64 oracle's state after k iterations from the
     energy-matched constant start (loaded through the checkpoint call)."""
@@ -117,7 +130,7 @@ def test_midrun_iteration_np128():
     _midrun_step(datagen.make_workload(dict(MID128, name="mid128"), seed=15), 5)
 
 
-@pytest.mark.parametrize("variant", [0, 2])
+@pytest.mark.parametrize("variant", [0, 2, 4])
 def test_midrun_iteration_np256_full_config(variant):
     _midrun_step(datagen.make_workload("p256", seed=3), 3, variant=variant)
 
