@@ -112,8 +112,10 @@ pmace_status pmace_get_image(pmace_handle h, float* out, int out_on_device, void
 /* The current patch stack v (J*Np*Np complex), host or device memory. */
 pmace_status pmace_get_patches(pmace_handle h, float* out, int out_on_device, void* stream);
 
-/* Residuals of the last iteration, computed on the device in FP64 in a fixed
- * order and returned in out[0..1]:
+/* Residuals of the last iteration (the last iteration of each pmace_iterate
+ * call writes the per-window partial sums; the ones before it skip that
+ * work), computed on the device in FP64 in a fixed order and returned in
+ * out[0..1]:
  *   out[0] = ||z_prev - w|| / ||w||: disagreement between the previous
  *            consensus stack and the new agent outputs (zero at the
  *            Algorithm 1 fixed point; z_prev = v before the first iteration);

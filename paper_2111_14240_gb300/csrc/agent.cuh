@@ -100,15 +100,17 @@ __device__ __forceinline__ float2 replace_magnitude(float2 xa, float y, float in
     return o;
 }
 
-// S4 + S5 for one pixel: g = F^* A' unnormalised, q and xv the pending
-// stack and consensus values, dv = 1/d ((0, 0) where d is treated as
-// absent).  v = q + 2 rho_prev xv; w = (alpha v + D^-1 g / Np) / (1 + alpha)
-// (w = v where d is absent); u = 2w - v; q' = v - 2 rho w.  Adds |z - w|^2
-// (z = v on the first iteration, else xv) and |w|^2 to the residual sums.
-__device__ __forceinline__ void agent_update(float2 g, float2 q, float2 xv, float2 dv, float two_rho_prev, float scale,
-                                             float alpha, float inv1pa, float two_rho, bool first, float2& u, float2& qn,
-                                             float& az, float& aw) {
-    const float2 v = make_float2(fmaf(two_rho_prev, xv.x, q.x), fmaf(two_rho_prev, xv.y, q.y));
+// S0 for one pixel: v = q + 2 rho_prev xv (closes the previous Mann step).
+__device__ __forceinline__ float2 mann_close(float2 q, float2 xv, float two_rho_prev) {
+    return make_float2(fmaf(two_rho_prev, xv.x, q.x), fmaf(two_rho_prev, xv.y, q.y));
+}
+
+// S4 + S5 for one pixel: g = F^* A' unnormalised, v the agent input, dv =
+// 1/d ((0, 0) where d is treated as absent).  w = (alpha v + D^-1 g / Np) /
+// (1 + alpha) (w = v where d is absent); u = 2w - v; q' = v - 2 rho w.
+// Returns w.
+__device__ __forceinline__ float2 agent_step(float2 g, float2 v, float2 dv, float scale, float alpha, float inv1pa,
+                                             float two_rho, float2& u, float2& qn) {
     float2 w;
     if (dv.x == 0.f && dv.y == 0.f) {
         w = v;                                    // d treated as absent here
@@ -118,7 +120,12 @@ __device__ __forceinline__ void agent_update(float2 g, float2 q, float2 xv, floa
     }
     u = make_float2(2.f * w.x - v.x, 2.f * w.y - v.y);
     qn = make_float2(fmaf(-two_rho, w.x, v.x), fmaf(-two_rho, w.y, v.y));
-    const float2 z = first ? v : xv;
+    return w;
+}
+
+// Residual sums of one pixel: |z - w|^2 and |w|^2 (z = v on the first
+// iteration, else the consensus value).
+__device__ __forceinline__ void residual_sums(float2 z, float2 w, float& az, float& aw) {
     const float dzx = z.x - w.x, dzy = z.y - w.y;
     az = fmaf(dzx, dzx, fmaf(dzy, dzy, az));
     aw = fmaf(w.x, w.x, fmaf(w.y, w.y, aw));
@@ -231,7 +238,7 @@ __device__ __forceinline__ void agent_body(const AgentArgs& a, const int j0) {
             continue;
         }
         const int2 off = a.offs[j0 + p];
-        const float2* qp = a.q + pbase_of(p);
+        float2* qp = a.q + pbase_of(p);   // q in, v out: the copy-out reads v back (same thread, same pair)
         const float2* __restrict__ xb = a.xbar + (size_t)(off.x + rank * R) * a.n2 + off.y;
         for_pairs<N, R, T, BATCH>([&](int i0) {
             float4 qv[BATCH], dv[BATCH];
@@ -249,8 +256,9 @@ __device__ __forceinline__ void agent_body(const AgentArgs& a, const int j0) {
             for (int i = 0; i < BATCH; ++i) {
                 const int t = threadIdx.x + (i0 + i) * T;
                 const int row = t / HALF, c = 2 * (t % HALF);
-                const float2 v0 = make_float2(fmaf(two_rho_prev, x0[i].x, qv[i].x), fmaf(two_rho_prev, x0[i].y, qv[i].y));
-                const float2 v1 = make_float2(fmaf(two_rho_prev, x1[i].x, qv[i].z), fmaf(two_rho_prev, x1[i].y, qv[i].w));
+                const float2 v0 = mann_close(make_float2(qv[i].x, qv[i].y), x0[i], two_rho_prev);
+                const float2 v1 = mann_close(make_float2(qv[i].z, qv[i].w), x1[i], two_rho_prev);
+                *reinterpret_cast<float4*>(qp + row * N + c) = make_float4(v0.x, v0.y, v1.x, v1.y);
                 float2* dst = tp + row * RS + pcol(c);
                 dst[0] = cmul(make_float2(dv[i].x, dv[i].y), v0);
                 dst[1] = cmul(make_float2(dv[i].z, dv[i].w), v1);
@@ -377,12 +385,13 @@ __device__ __forceinline__ void agent_body(const AgentArgs& a, const int j0) {
         const float alpha = a.alpha;
         const float two_rho = 2.0f * a.rho_cur;
         const bool first = a.first != 0;
+        const bool res = a.residual != 0;
 #pragma unroll
         for (int p = 0; p < PPC; ++p) {
             float az = 0.f, aw = 0.f;
             if (valid(p)) {
                 const int2 off = a.offs[j0 + p];
-                float2* qp = a.q + pbase_of(p);   // read (S0) and overwritten (S5) pair by pair by one thread
+                float2* qp = a.q + pbase_of(p);   // v (written by the copy-in), overwritten by q' pair by pair by one thread
                 float2* __restrict__ uo = a.u + pbase_of(p);
                 const float2* __restrict__ xb = a.xbar + (size_t)(off.x + rank * R) * a.n2 + off.y;
                 const float2* tp = tile + p * R * RS;
@@ -395,19 +404,26 @@ __device__ __forceinline__ void agent_body(const AgentArgs& a, const int j0) {
                         const int row = t / HALF, c = 2 * (t % HALF);
                         qv[i] = *reinterpret_cast<const float4*>(qp + row * N + c);
                         dv[i] = __ldg(reinterpret_cast<const float4*>(di + row * N + c));
-                        x0[i] = __ldg(xb + (size_t)row * a.n2 + c);
-                        x1[i] = __ldg(xb + (size_t)row * a.n2 + c + 1);
+                        if (res) {   // the consensus values only feed the residual now
+                            x0[i] = __ldg(xb + (size_t)row * a.n2 + c);
+                            x1[i] = __ldg(xb + (size_t)row * a.n2 + c + 1);
+                        }
                     }
 #pragma unroll
                     for (int i = 0; i < BATCH_OUT; ++i) {
                         const int t = threadIdx.x + (i0 + i) * T;
                         const int row = t / HALF, c = 2 * (t % HALF);
                         const float2* src = tp + row * RS + pcol(c);
+                        const float2 v0 = make_float2(qv[i].x, qv[i].y), v1 = make_float2(qv[i].z, qv[i].w);
                         float2 u0, u1, q0, q1;
-                        agent_update(src[0], make_float2(qv[i].x, qv[i].y), x0[i], make_float2(dv[i].x, dv[i].y),
-                                     two_rho_prev, scale, alpha, inv1pa, two_rho, first, u0, q0, az, aw);
-                        agent_update(src[1], make_float2(qv[i].z, qv[i].w), x1[i], make_float2(dv[i].z, dv[i].w),
-                                     two_rho_prev, scale, alpha, inv1pa, two_rho, first, u1, q1, az, aw);
+                        const float2 w0 = agent_step(src[0], v0, make_float2(dv[i].x, dv[i].y), scale, alpha, inv1pa,
+                                                     two_rho, u0, q0);
+                        const float2 w1 = agent_step(src[1], v1, make_float2(dv[i].z, dv[i].w), scale, alpha, inv1pa,
+                                                     two_rho, u1, q1);
+                        if (res) {
+                            residual_sums(first ? v0 : x0[i], w0, az, aw);
+                            residual_sums(first ? v1 : x1[i], w1, az, aw);
+                        }
                         *reinterpret_cast<float4*>(uo + row * N + c) = make_float4(u0.x, u0.y, u1.x, u1.y);
                         *reinterpret_cast<float4*>(qp + row * N + c) = make_float4(q0.x, q0.y, q1.x, q1.y);
                     }
@@ -417,6 +433,7 @@ __device__ __forceinline__ void agent_body(const AgentArgs& a, const int j0) {
             acc_w[p] = aw;
         }
     }
+    if (a.residual == 0) return;      // only the residual iteration writes partial sums
 #pragma unroll
     for (int p = 0; p < PPC; ++p) {
         float acc[4] = {acc_z[p], acc_w[p], acc_d[p], acc_y[p]};

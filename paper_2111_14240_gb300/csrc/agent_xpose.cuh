@@ -155,6 +155,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
     const float alpha = a.alpha;
     const float two_rho = 2.0f * a.rho_cur;
     const bool first = a.first != 0;
+    const bool res = a.residual != 0;
     const int row0 = rank * G::R;
     uint32_t parity = 0;
 
@@ -188,10 +189,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
 #pragma unroll
             for (int t = 0; t < r1; ++t) x[t] = qr[b + S1 * t];
 #pragma unroll
-            for (int t = 0; t < r1; ++t) {
-                const float2 xv = __ldg(xr + b + S1 * t);
-                x[t] = make_float2(fmaf(two_rho_prev, xv.x, x[t].x), fmaf(two_rho_prev, xv.y, x[t].y));
-            }
+            for (int t = 0; t < r1; ++t) x[t] = mann_close(x[t], __ldg(xr + b + S1 * t), two_rho_prev);
 #pragma unroll
             for (int t = 0; t < r1; ++t) x[t] = cmul(__ldg(dr + b + S1 * t), x[t]);
             Dft<r1, false>::run(x);
@@ -336,15 +334,17 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
                 for (int t = 0; t < H; ++t) {
                     const int s = b + S1 * (h0 + t);
                     float2 u, qn;
-                    agent_update(x[h0 + t], qv[t], xv[t], dv[t], two_rho_prev, scale, alpha, inv1pa, two_rho, first,
-                                 u, qn, acc_z, acc_w);
+                    const float2 v = mann_close(qv[t], xv[t], two_rho_prev);
+                    const float2 w = agent_step(x[h0 + t], v, dv[t], scale, alpha, inv1pa, two_rho, u, qn);
+                    if (res) residual_sums(first ? v : xv[t], w, acc_z, acc_w);
                     ur[s] = u;
                     qr[s] = qn;
                 }
             }
         }
         float acc[4] = {acc_z, acc_w, acc_d, acc_y};
-        block_reduce4<T>(acc, red, a.partials + ((size_t)j * C + rank) * 4);
+        if (res) block_reduce4<T>(acc, red, a.partials + ((size_t)j * C + rank) * 4);
+        else __syncthreads();   // the next window's copy-in overwrites A
         parity ^= 1u;
     }
     cl.sync();   // every copy into this CTA has landed; no peer still reads from it

@@ -472,6 +472,7 @@ AgentArgs agent_args(const pmace_job* h, float alpha, float rho) {
     a.first = h->iterations == 0 ? 1 : 0;
     a.wpc = h->wpc;
     a.err = h->err;
+    a.residual = 1;
     return a;
 }
 }  // namespace pmace
@@ -479,9 +480,11 @@ AgentArgs agent_args(const pmace_job* h, float alpha, float rho) {
 namespace {
 
 
-// One iteration of Algorithm 1: agent sweep (S0-S5) then consensus (S6).
-pmace_status launch_iteration(pmace_job* h, float alpha, float rho, cudaStream_t s, bool events) {
-    const AgentArgs a = agent_args(h, alpha, rho);
+// One iteration of Algorithm 1: agent sweep (S0-S5) then consensus (S6);
+// `residual`: the sweep also writes the residual partial sums.
+pmace_status launch_iteration(pmace_job* h, float alpha, float rho, cudaStream_t s, bool events, bool residual) {
+    AgentArgs a = agent_args(h, alpha, rho);
+    a.residual = residual ? 1 : 0;
     GatherArgs g = gather_args(h);
     g.src = h->u;
     g.out = h->xbar;
@@ -514,7 +517,8 @@ pmace_status ensure_graph(pmace_job* h, float alpha, float rho) {
     cudaGraph_t graph = nullptr;
     PM_CUDA(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
     pmace_status st = PMACE_OK;
-    for (int i = 0; i < kGraphIters && st == PMACE_OK; ++i) st = launch_iteration(h, alpha, rho, h->capture_stream, false);
+    for (int i = 0; i < kGraphIters && st == PMACE_OK; ++i)
+        st = launch_iteration(h, alpha, rho, h->capture_stream, false, false);
     cudaError_t e = cudaStreamEndCapture(h->capture_stream, &graph);
     h->iterations = it_saved;
     h->rho_pending = rho_saved;
@@ -787,21 +791,23 @@ pmace_status pmace_iterate(pmace_handle h, int32_t n, const pmace_step* step, vo
     // Iterations that open with the pending rho of an earlier call (or the
     // job's first iteration) are launched directly; the steady state
     // (rho_prev == rho) replays a captured graph of kGraphIters iterations.
+    // Only the call's last iteration, always launched directly, writes the
+    // residual partial sums that pmace_residual reduces.
     while (done < n && (h->iterations == 0 || h->rho_pending != rho)) {
-        pmace_status st = launch_iteration(h, alpha, rho, s, h->profiling);
+        pmace_status st = launch_iteration(h, alpha, rho, s, h->profiling, done + 1 == n);
         if (st != PMACE_OK) return st;
         ++done;
     }
-    if (!h->profiling && h->use_graphs && n - done >= kGraphIters) {
+    if (!h->profiling && h->use_graphs && n - 1 - done >= kGraphIters) {
         pmace_status st = ensure_graph(h, alpha, rho);
         if (st != PMACE_OK) return st;
-        for (; done + kGraphIters <= n; done += kGraphIters) {
+        for (; done + kGraphIters <= n - 1; done += kGraphIters) {
             PM_CUDA(h, cudaGraphLaunch(h->graph, s));
             h->iterations += kGraphIters;
         }
     }
     for (; done < n; ++done) {
-        pmace_status st = launch_iteration(h, alpha, rho, s, h->profiling);
+        pmace_status st = launch_iteration(h, alpha, rho, s, h->profiling, done + 1 == n);
         if (st != PMACE_OK) return st;
     }
     return PMACE_OK;

@@ -24,7 +24,8 @@ __host__ __device__ constexpr RadixPlan radix_plan(int L) {
 
 // Arguments of one agent sweep (steps S0-S5 of one iteration, all patches).
 struct AgentArgs {
-    float2* q;              // [J][Np][Np] pending stack q = v - 2 rho w (read, then overwritten)
+    float2* q;              // [J][Np][Np] pending stack q = v - 2 rho w (read, then overwritten; the
+                            // in-place variant keeps v there between its copy-in and copy-out)
     float2* u;              // [J][Np][Np] written: u = 2w - v
     const float2* xbar;     // [n1][n2] consensus image of the previous iteration
     const void* y;          // [J][Np][Np] amplitudes in kernel (digit-reversed) order
@@ -38,6 +39,7 @@ struct AgentArgs {
     int J;
     float alpha, rho_prev, rho_cur;
     int first;              // 1 on the first iteration of the job
+    int residual;           // 1: write the residual partial sums (else they are left untouched)
     int wpc;                // windows per cluster (transposing-exchange variant)
     int* err;               // bit 2 set when a bounded device-side wait gives up
 };

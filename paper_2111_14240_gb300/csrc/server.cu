@@ -284,6 +284,7 @@ pmace_status pmace_server::tick() {
             const Active& a = active[i];
             const int jd = (int)adesc.size();
             adesc.push_back(agent_args(a.job, a.req.step.alpha, a.req.step.rho));
+            adesc.back().residual = a.job->iterations + 1 >= a.req.iterations ? 1 : 0;   // the job's last iteration
             for (int j0 = 0; j0 < a.job->dims.J; j0 += a.job->wpc) awork.push_back(make_int2(jd, j0));
             stepping.push_back(i);
         }
