@@ -342,9 +342,11 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
                 }
             }
         }
+        // No barrier is needed before the next window: its copy-in writes
+        // exactly the A rows this thread's warp has just read (the same
+        // (k, b) butterflies), and the reduction buffer is only used here.
         float acc[4] = {acc_z, acc_w, acc_d, acc_y};
         if (res) block_reduce4<T>(acc, red, a.partials + ((size_t)j * C + rank) * 4);
-        else __syncthreads();   // the next window's copy-in overwrites A
         parity ^= 1u;
     }
     cl.sync();   // every copy into this CTA has landed; no peer still reads from it
