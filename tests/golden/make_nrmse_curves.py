@@ -1,0 +1,49 @@
+"""Write the FP64 oracle's reconstruction-error curves used by the GPU tests.
+
+Runs Algorithm 1 of the oracle (and nothing else) on seeded synthetic
+workloads from the energy-matched constant start and records the NRMSE of
+Section IV (global phase aligned, over the pixels some window covers) of
+the readout x_hat after every `every` iterations.  Usage:
+
+    python tests/golden/make_nrmse_curves.py
+
+writes tests/golden/nrmse_<name>.json.  Deterministic: the workloads come
+from seeded generators and the oracle is plain FP64 numpy.
+"""
+import json
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.join(HERE, "..", ".."))
+
+from oracle import pmace_oracle as orc  # noqa: E402
+from paper_2111_14240_gb300 import datagen  # noqa: E402
+
+# (workload, seed, iterations, every, alpha, rho, kappa)
+CURVES = [("p256", 1, 100, 10, 0.5, 0.5, 1.25)]
+
+
+def curve(name, seed, iters, every, alpha, rho, kappa):
+    w = datagen.make_workload(name, seed=seed)
+    mask = orc.weight_image(w.probe, w.offsets, w.x.shape, kappa) > 0
+    v = z = None
+    points = []
+    for k in range(every, iters + 1, every):
+        o = orc.pmace(w.y, w.probe, w.offsets, w.x.shape, alpha=alpha, rho=rho, kappa=kappa,
+                      n_iter=every, v0=v, z_prev=z)
+        v, z = o["v"], o["z"]
+        points.append(dict(iteration=k, nrmse=orc.nrmse(o["x_hat"], w.x, mask), r_fp=o["r_fp"],
+                           r_data=o["r_data"]))
+        print(name, points[-1], flush=True)
+    return dict(workload=name, seed=seed, alpha=alpha, rho=rho, kappa=kappa,
+                start="energy-matched constant", points=points)
+
+
+if __name__ == "__main__":
+    for spec in CURVES:
+        d = curve(*spec)
+        with open(os.path.join(HERE, f"nrmse_{spec[0]}.json"), "w") as f:
+            json.dump(d, f, indent=1)
