@@ -39,6 +39,8 @@
 #pragma once
 
 #include "agent.cuh"
+#include "cache_hints.cuh"
+#include "tmem.cuh"
 
 namespace pmace {
 
@@ -119,8 +121,10 @@ __device__ __forceinline__ void mbar_wait_bounded(uint32_t bar, uint32_t parity,
     if (err) atomicOr(err, 2);
 }
 
-// Windows j0 .. jn - 1 of the job `a` on one cluster.
-template <int N, int AMP>
+// Windows j0 .. jn - 1 of the job `a` on one cluster.  TMC: keep d and 1/d
+// in TMEM where the geometry allows (the launched kernels); the twin
+// without it only serves the occupancy query (see agent_xpose).
+template <int N, int AMP, bool TMC>
 __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, const int jn) {
     using G = XposeGeom<N>;
     constexpr int C = G::C, T = G::kThreads, r1 = G::r1, r2 = G::r2, S1 = G::S1;
@@ -157,7 +161,43 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
     const bool first = a.first != 0;
     const bool res = a.residual != 0;
     const int row0 = rank * G::R;
+    const uint64_t pol_u = a.keep_u ? l2_policy_evict_last() : l2_policy_evict_normal();
+    const uint64_t pol_first = l2_policy_evict_first();
     uint32_t parity = 0;
+
+    // With one first-stage butterfly per thread (Np >= 128), a thread's 16
+    // values of d (copy-in) and of 1/d (copy-out) are the same in every
+    // window: they are kept in TMEM, 64 columns of the thread's lane.
+    constexpr bool kTm = TMC && G::NB1 == T && r1 == 16;
+    constexpr uint32_t kTmCols = kTm ? 64u * (uint32_t)((T / 32 + 3) / 4) : 32u;
+    static_assert(!kTm || kTmCols * G::kBySmem <= 512, "TMEM of the resident CTAs must fit an SM");
+    __shared__ uint32_t tm_sh;
+    uint32_t tm_addr = 0;
+    if constexpr (kTm) {
+        if (threadIdx.x < 32) tmem_alloc(smem_addr(&tm_sh), kTmCols);
+        tmem_fence_before_sync();
+        __syncthreads();
+        tmem_fence_after_sync();
+        const int warp = threadIdx.x >> 5;
+        tm_addr = tm_sh + ((uint32_t)(32 * (warp & 3)) << 16) + 64u * (uint32_t)(warp >> 2);
+        const int k = threadIdx.x / S1, b = threadIdx.x % S1;
+        const float2* tabs[2] = {a.probe + (size_t)(row0 + k) * N, a.dinv + (size_t)(row0 + k) * N};
+#pragma unroll
+        for (int tab = 0; tab < 2; ++tab) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t r[16];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const float2 d = __ldg(tabs[tab] + b + S1 * (8 * h + t));
+                    r[2 * t] = __float_as_uint(d.x);
+                    r[2 * t + 1] = __float_as_uint(d.y);
+                }
+                tmem_st16(tm_addr + 32u * tab + 16u * h, r);
+            }
+        }
+        tmem_wait_st();
+    }
 
     // the CTA's stack rows and amplitude rows of a window (one thread each)
     auto prefetch_window = [&](int jw) {
@@ -190,8 +230,19 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
             for (int t = 0; t < r1; ++t) x[t] = qr[b + S1 * t];
 #pragma unroll
             for (int t = 0; t < r1; ++t) x[t] = mann_close(x[t], __ldg(xr + b + S1 * t), two_rho_prev);
+            if constexpr (kTm) {
 #pragma unroll
-            for (int t = 0; t < r1; ++t) x[t] = cmul(__ldg(dr + b + S1 * t), x[t]);
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t r[16];
+                    tmem_ld16(tm_addr + 16u * h, r);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t)
+                        x[8 * h + t] = cmul(make_float2(__uint_as_float(r[2 * t]), __uint_as_float(r[2 * t + 1])), x[8 * h + t]);
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < r1; ++t) x[t] = cmul(__ldg(dr + b + S1 * t), x[t]);
+            }
             Dft<r1, false>::run(x);
 #pragma unroll
             for (int t = 1; t < r1; ++t) x[t] = cmul(x[t], tw[b * t]);
@@ -227,7 +278,15 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
             const int id = threadIdx.x + u * T;
             const int c = id % 16, m = id / 16;
 #pragma unroll
-            for (int i = 0; i < r2; ++i) yv[u][i] = load_amp<AMP>(a.y, wbase + (size_t)(m * r2 + i) * N + row0 + c, yscale);
+            for (int i = 0; i < r2; ++i) {
+                const size_t yi = wbase + (size_t)(m * r2 + i) * N + row0 + c;
+                if constexpr (AMP == 0) {
+                    yv[u][i] = ld_nc_l2_hint(static_cast<const float*>(a.y) + yi, pol_first);
+                } else {
+                    const unsigned short h = ld_nc_l2_hint(static_cast<const unsigned short*>(a.y) + yi, pol_first);
+                    yv[u][i] = __half2float(__ushort_as_half(h)) * yscale;
+                }
+            }
         }
         mbar_wait_bounded(bar_b, parity, a.err);
         // re-arm for the next window before this CTA's next send: every
@@ -328,7 +387,14 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
                     const int s = b + S1 * (h0 + t);
                     qv[t] = qr[s];
                     xv[t] = __ldg(xr + s);
-                    dv[t] = __ldg(dr + s);
+                    if constexpr (!kTm) dv[t] = __ldg(dr + s);
+                }
+                if constexpr (kTm) {
+                    static_assert(H == 4, "one 8-column TMEM load per quarter");
+                    uint32_t r[8];
+                    tmem_ld8(tm_addr + 32u + 2u * (uint32_t)h0, r);
+#pragma unroll
+                    for (int t = 0; t < H; ++t) dv[t] = make_float2(__uint_as_float(r[2 * t]), __uint_as_float(r[2 * t + 1]));
                 }
 #pragma unroll
                 for (int t = 0; t < H; ++t) {
@@ -337,8 +403,8 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
                     const float2 v = mann_close(qv[t], xv[t], two_rho_prev);
                     const float2 w = agent_step(x[h0 + t], v, dv[t], scale, alpha, inv1pa, two_rho, u, qn);
                     if (res) residual_sums(first ? v : xv[t], w, acc_z, acc_w);
-                    ur[s] = u;
-                    qr[s] = qn;
+                    st_l2_hint(ur + s, u, pol_u);       // read by the consensus gather next
+                    st_l2_hint(qr + s, qn, pol_first);  // read again only next iteration
                 }
             }
         }
@@ -349,15 +415,22 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
         if (res) block_reduce4<T>(acc, red, a.partials + ((size_t)j * C + rank) * 4);
         parity ^= 1u;
     }
+    if constexpr (kTm) tmem_fence_before_sync();
     cl.sync();   // every copy into this CTA has landed; no peer still reads from it
+    if constexpr (kTm) {
+        if (threadIdx.x < 32) {
+            tmem_fence_after_sync();
+            tmem_dealloc(tm_sh, kTmCols);
+        }
+    }
 }
 
 // One job: cluster k processes windows [k wpc, min((k + 1) wpc, J)).
-template <int N, int AMP>
+template <int N, int AMP, bool TMC = true>
 __global__ void __launch_bounds__(XposeGeom<N>::kThreads, XposeGeom<N>::kMinBlocks)
 agent_xpose_kernel(const __grid_constant__ AgentArgs a) {
     const int j0 = (int)(blockIdx.x / XposeGeom<N>::C) * a.wpc;
-    xpose_body<N, AMP>(a, j0, min(j0 + a.wpc, a.J));
+    xpose_body<N, AMP, TMC>(a, j0, min(j0 + a.wpc, a.J));
 }
 
 // Several jobs: cluster k processes job work[k].x from window work[k].y on,
@@ -367,7 +440,7 @@ __global__ void __launch_bounds__(XposeGeom<N>::kThreads, XposeGeom<N>::kMinBloc
 agent_xpose_kernel_batched(const AgentArgs* __restrict__ descs, const int2* __restrict__ work) {
     const int2 w = work[blockIdx.x / XposeGeom<N>::C];
     const AgentArgs& a = descs[w.x];
-    xpose_body<N, AMP>(a, w.y, min(w.y + a.wpc, a.J));
+    xpose_body<N, AMP, true>(a, w.y, min(w.y + a.wpc, a.J));
 }
 
 template <int N, typename K>
@@ -402,14 +475,20 @@ cudaError_t agent_xpose(const AgentArgs* a, int amp_f16, cudaStream_t s, AgentPl
     void (*fn)(const AgentArgs) = amp_f16 ? agent_xpose_kernel<N, 1> : agent_xpose_kernel<N, 0>;
     cudaError_t e = xpose_attributes(fn, G::kSmem, G::C);
     if (a == nullptr) {
+        // The occupancy API counts a kernel that allocates TMEM as one CTA
+        // per SM.  The TMEM cache takes at most 1.9 columns per KB of shared
+        // memory, so 426 of an SM's 512 columns in any mix of resident CTAs,
+        // and never limits residency: ask for the same kernel without it.
+        void (*twin)(const AgentArgs) = agent_xpose_kernel<N, 0, false>;
+        cudaError_t et = xpose_attributes(twin, G::kSmem, G::C);
         info->threads = G::kThreads;
         info->smem_bytes = G::kSmem;
         info->max_clusters = 0;
-        if (e == cudaSuccess) {
+        if (e == cudaSuccess && et == cudaSuccess) {
             cudaLaunchAttribute attr[1];
-            cudaLaunchConfig_t cfg = xpose_config<N>(fn, 64, nullptr, attr);
+            cudaLaunchConfig_t cfg = xpose_config<N>(twin, 64, nullptr, attr);
             int n = 0;
-            if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess) info->max_clusters = n;
+            if (cudaOccupancyMaxActiveClusters(&n, twin, &cfg) == cudaSuccess) info->max_clusters = n;
         }
         cudaGetLastError();
         info->launchable = info->max_clusters > 0;

@@ -1,0 +1,50 @@
+// L2 eviction-priority hints for the two streams that meet in L2 within one
+// iteration: the agent sweep writes u, which the consensus gather reads
+// right after, while q', the amplitudes and the stack reads of the sweep are
+// used once per iteration.  u is stored evict-last, the single-use streams
+// are marked evict-first, so more of u is still in L2 when the gather runs.
+// The evict-last hint is only given where u can mostly stay in L2 (a job's
+// u no larger than twice the L2), else u is stored evict-normal.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pmace {
+
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_normal() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void st_l2_hint(float2* ptr, float2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(ptr), "f"(v.x), "f"(v.y), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ float2 ld_nc_l2_hint(const float2* ptr, uint64_t pol) {
+    float2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ld_nc_l2_hint(const float* ptr, uint64_t pol) {
+    float v;
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ unsigned short ld_nc_l2_hint(const unsigned short* ptr, uint64_t pol) {
+    unsigned short v;
+    asm volatile("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+
+}  // namespace pmace

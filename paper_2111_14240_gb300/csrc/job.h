@@ -25,6 +25,7 @@ struct pmace_job {
     int cluster = 1;
     int variant = 0;
     int wpc = 1;              // windows per agent cluster
+    int keep_u = 0;           // u small enough to favour it in L2 for the gather
     pmace::AgentPlanInfo plan{};
     int tiles_x = 0, tiles_y = 0, ntiles = 0;
     int tile_h = 16;          // gather tile height (rows), width kGatherTileW

@@ -148,7 +148,8 @@ std::vector<int> amp_row_order(int np, int variant) {
 
 // Windows each agent cluster processes: the variant's own count, or for the
 // transposing exchange (a run of windows per cluster) J spread evenly over
-// the clusters the device holds at once (PMACE_AGENT_WPC fixes the run).
+// twice the clusters the device holds at once, so that clusters that finish
+// early take up the remaining runs (PMACE_AGENT_WPC fixes the run).
 int windows_per_cluster(int np, int variant, int J, const AgentPlanInfo& info) {
     const AgentVariant v = agent_variant_of(np, variant);
     if (!v.exchange) return v.windows;
@@ -156,7 +157,7 @@ int windows_per_cluster(int np, int variant, int J, const AgentPlanInfo& info) {
         const int w = std::atoi(env);
         if (w > 0) return w;
     }
-    const int m = std::max(info.max_clusters, 1);
+    const int m = 2 * std::max(info.max_clusters, 1);
     return std::max(1, (J + m - 1) / m);
 }
 
@@ -473,6 +474,7 @@ AgentArgs agent_args(const pmace_job* h, float alpha, float rho) {
     a.wpc = h->wpc;
     a.err = h->err;
     a.residual = 1;
+    a.keep_u = h->keep_u;
     return a;
 }
 }  // namespace pmace
@@ -649,6 +651,11 @@ pmace_status pmace_create(const pmace_dims* dims, const float* probe, const int3
     h->dims = D;
     h->amp_f16 = fmt == PMACE_AMP_F16_SCALED;
     cudaGetDevice(&h->device);
+    {
+        int l2 = 0;
+        if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device) != cudaSuccess) cudaGetLastError();
+        h->keep_u = l2 > 0 && JP * sizeof(float2) <= 2 * (size_t)l2;
+    }
 
     auto bail = [&](pmace_status st) {
         g_create_error = h->error;

@@ -40,6 +40,7 @@ struct AgentArgs {
     float alpha, rho_prev, rho_cur;
     int first;              // 1 on the first iteration of the job
     int residual;           // 1: write the residual partial sums (else they are left untouched)
+    int keep_u;             // 1: store u with the L2 evict-last hint (u fits about twice the L2)
     int wpc;                // windows per cluster (transposing-exchange variant)
     int* err;               // bit 2 set when a bounded device-side wait gives up
 };

@@ -3,6 +3,7 @@
 // readout, the amplitude layout pass, the deterministic FP64 reduction of the
 // residual partials, and the stack initialisation of Algorithm 1.
 #include "pmace_internal.h"
+#include "cache_hints.cuh"
 
 #include <cuda_fp16.h>
 
@@ -43,6 +44,7 @@ __device__ __forceinline__ void gather_body(const GatherArgs& g, const int unit)
     const int np = g.np;
     const size_t P = (size_t)np * np;
 
+    const uint64_t pol_first = l2_policy_evict_first();   // u: this is its last read
     using Acc = typename std::conditional<MODE == 0, double, float2>::type;
     Acc acc[RPT];
 #pragma unroll
@@ -81,7 +83,8 @@ __device__ __forceinline__ void gather_body(const GatherArgs& g, const int unit)
                     if (inx && (unsigned)ly < (unsigned)np) {
                         const int e = ly * np + lx;
                         wgt[k][r] = __ldg(g.wk + e);
-                        if constexpr (MODE != 0) val[k][r] = __ldg(g.src + (size_t)i * P + e);
+                        if constexpr (MODE == 1) val[k][r] = ld_nc_l2_hint(g.src + (size_t)i * P + e, pol_first);
+                        else if constexpr (MODE == 2) val[k][r] = __ldg(g.src + (size_t)i * P + e);
                     }
                 }
             }
