@@ -42,7 +42,8 @@ WORKLOAD = ("p256: object 600x600 complex64, probe 256x256 (Gaussian sigma 48 px
             "Poisson peak 1e5, alpha 0.5, rho 0.5, kappa 1.25")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "agent_p256_traffic.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2111_14240_gb300", "csrc", f)
-                  for f in ("agent.cuh", "agent_xpose.cuh", "fft_smem.cuh", "pmace_internal.h")]
+                  for f in ("agent.cuh", "agent_xpose.cuh", "cache_hints.cuh", "tmem.cuh", "fft_smem.cuh",
+                            "pmace_internal.h")]
 
 
 def kernel_hash() -> str:

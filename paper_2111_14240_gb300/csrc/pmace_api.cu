@@ -147,9 +147,10 @@ std::vector<int> amp_row_order(int np, int variant) {
 }
 
 // Windows each agent cluster processes: the variant's own count, or for the
-// transposing exchange (a run of windows per cluster) J spread evenly over
-// twice the clusters the device holds at once, so that clusters that finish
-// early take up the remaining runs (PMACE_AGENT_WPC fixes the run).
+// transposing exchange (a run of windows per cluster) J spread over four
+// times the clusters the device holds at once, and at most 8: short runs let
+// the clusters that finish early take up the remaining ones, which balances
+// SMs that hold different numbers of CTAs (PMACE_AGENT_WPC fixes the run).
 int windows_per_cluster(int np, int variant, int J, const AgentPlanInfo& info) {
     const AgentVariant v = agent_variant_of(np, variant);
     if (!v.exchange) return v.windows;
@@ -157,8 +158,8 @@ int windows_per_cluster(int np, int variant, int J, const AgentPlanInfo& info) {
         const int w = std::atoi(env);
         if (w > 0) return w;
     }
-    const int m = 2 * std::max(info.max_clusters, 1);
-    return std::max(1, (J + m - 1) / m);
+    const int m = 4 * std::max(info.max_clusters, 1);
+    return std::max(1, std::min(8, (J + m - 1) / m));
 }
 
 // Gather tables of one tile height: for every tile_h x kGatherTileW image
