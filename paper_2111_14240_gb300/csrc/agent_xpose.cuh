@@ -166,8 +166,10 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
     uint32_t parity = 0;
 
     // With one first-stage butterfly per thread (Np >= 128), a thread's 16
-    // values of d (copy-in) and of 1/d (copy-out) are the same in every
-    // window: they are kept in TMEM, 64 columns of the thread's lane.
+    // values of 1/d are the same in every window and its 16 values of v are
+    // needed again in the copy-out of the same window: both are kept in
+    // TMEM, 64 columns of the thread's lane (1/d in 0..31, v in 32..63), so
+    // the copy-out loads nothing from memory outside the residual iteration.
     constexpr bool kTm = TMC && G::NB1 == T && r1 == 16;
     constexpr uint32_t kTmCols = kTm ? 64u * (uint32_t)((T / 32 + 3) / 4) : 32u;
     static_assert(!kTm || kTmCols * G::kBySmem <= 512, "TMEM of the resident CTAs must fit an SM");
@@ -181,20 +183,17 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
         const int warp = threadIdx.x >> 5;
         tm_addr = tm_sh + ((uint32_t)(32 * (warp & 3)) << 16) + 64u * (uint32_t)(warp >> 2);
         const int k = threadIdx.x / S1, b = threadIdx.x % S1;
-        const float2* tabs[2] = {a.probe + (size_t)(row0 + k) * N, a.dinv + (size_t)(row0 + k) * N};
+        const float2* dr = a.dinv + (size_t)(row0 + k) * N;
 #pragma unroll
-        for (int tab = 0; tab < 2; ++tab) {
+        for (int h = 0; h < 2; ++h) {
+            uint32_t r[16];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                uint32_t r[16];
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const float2 d = __ldg(tabs[tab] + b + S1 * (8 * h + t));
-                    r[2 * t] = __float_as_uint(d.x);
-                    r[2 * t + 1] = __float_as_uint(d.y);
-                }
-                tmem_st16(tm_addr + 32u * tab + 16u * h, r);
+            for (int t = 0; t < 8; ++t) {
+                const float2 d = __ldg(dr + b + S1 * (8 * h + t));
+                r[2 * t] = __float_as_uint(d.x);
+                r[2 * t + 1] = __float_as_uint(d.y);
             }
+            tmem_st16(tm_addr + 16u * h, r);
         }
         tmem_wait_st();
     }
@@ -232,17 +231,18 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
             for (int t = 0; t < r1; ++t) x[t] = mann_close(x[t], __ldg(xr + b + S1 * t), two_rho_prev);
             if constexpr (kTm) {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
+                for (int h = 0; h < 2; ++h) {   // keep v for the copy-out
                     uint32_t r[16];
-                    tmem_ld16(tm_addr + 16u * h, r);
 #pragma unroll
-                    for (int t = 0; t < 8; ++t)
-                        x[8 * h + t] = cmul(make_float2(__uint_as_float(r[2 * t]), __uint_as_float(r[2 * t + 1])), x[8 * h + t]);
+                    for (int t = 0; t < 8; ++t) {
+                        r[2 * t] = __float_as_uint(x[8 * h + t].x);
+                        r[2 * t + 1] = __float_as_uint(x[8 * h + t].y);
+                    }
+                    tmem_st16(tm_addr + 32u + 16u * h, r);
                 }
-            } else {
-#pragma unroll
-                for (int t = 0; t < r1; ++t) x[t] = cmul(__ldg(dr + b + S1 * t), x[t]);
             }
+#pragma unroll
+            for (int t = 0; t < r1; ++t) x[t] = cmul(__ldg(dr + b + S1 * t), x[t]);
             Dft<r1, false>::run(x);
 #pragma unroll
             for (int t = 1; t < r1; ++t) x[t] = cmul(x[t], tw[b * t]);
@@ -379,28 +379,37 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
             const float2* __restrict__ xr = a.xbar + (size_t)(off.x + row) * a.n2 + off.y;
             // in quarters: the loads of a quarter are issued together
             constexpr int H = r1 / 4;
+            if constexpr (kTm) tmem_wait_st();   // v of the copy-in has landed
 #pragma unroll
             for (int h0 = 0; h0 < r1; h0 += H) {
                 float2 qv[H], xv[H], dv[H];
-#pragma unroll
-                for (int t = 0; t < H; ++t) {
-                    const int s = b + S1 * (h0 + t);
-                    qv[t] = qr[s];
-                    xv[t] = __ldg(xr + s);
-                    if constexpr (!kTm) dv[t] = __ldg(dr + s);
-                }
                 if constexpr (kTm) {
-                    static_assert(H == 4, "one 8-column TMEM load per quarter");
-                    uint32_t r[8];
-                    tmem_ld8(tm_addr + 32u + 2u * (uint32_t)h0, r);
+                    // v and 1/d from TMEM; the consensus values only feed the residual
+                    static_assert(H == 4, "one 8-column TMEM load per quarter and table");
+                    uint32_t rv[8], rd[8];
+                    tmem_ld8(tm_addr + 32u + 2u * (uint32_t)h0, rv);
+                    tmem_ld8(tm_addr + 2u * (uint32_t)h0, rd);
 #pragma unroll
-                    for (int t = 0; t < H; ++t) dv[t] = make_float2(__uint_as_float(r[2 * t]), __uint_as_float(r[2 * t + 1]));
+                    for (int t = 0; t < H; ++t) {
+                        qv[t] = make_float2(__uint_as_float(rv[2 * t]), __uint_as_float(rv[2 * t + 1]));
+                        dv[t] = make_float2(__uint_as_float(rd[2 * t]), __uint_as_float(rd[2 * t + 1]));
+                        if (res) xv[t] = __ldg(xr + b + S1 * (h0 + t));
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < H; ++t) {
+                        const int s = b + S1 * (h0 + t);
+                        qv[t] = qr[s];
+                        xv[t] = __ldg(xr + s);
+                        dv[t] = __ldg(dr + s);
+                    }
                 }
 #pragma unroll
                 for (int t = 0; t < H; ++t) {
                     const int s = b + S1 * (h0 + t);
                     float2 u, qn;
-                    const float2 v = mann_close(qv[t], xv[t], two_rho_prev);
+                    // v: kept from the copy-in (TMEM), else q + 2 rho_prev xbar again
+                    const float2 v = kTm ? qv[t] : mann_close(qv[t], xv[t], two_rho_prev);
                     const float2 w = agent_step(x[h0 + t], v, dv[t], scale, alpha, inv1pa, two_rho, u, qn);
                     if (res) residual_sums(first ? v : xv[t], w, acc_z, acc_w);
                     st_l2_hint(ur + s, u, pol_u);       // read by the consensus gather next
