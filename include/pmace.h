@@ -286,7 +286,8 @@ const char* pmace_last_error(pmace_handle h);
 
 const char* pmace_status_string(pmace_status s);
 
-/* ABI version, bumped on any incompatible change. */
+/* ABI version, bumped on any incompatible change (2: pmace_plan gained the
+ * exchange and windows_per_cluster fields). */
 int32_t pmace_abi_version(void);
 
 #ifdef __cplusplus

@@ -592,7 +592,7 @@ pmace_status switch_plan(pmace_job* h, int variant, int tile_h, cudaStream_t s) 
 
 extern "C" {
 
-int32_t pmace_abi_version(void) { return 1; }
+int32_t pmace_abi_version(void) { return 2; }
 
 const char* pmace_status_string(pmace_status s) {
     switch (s) {

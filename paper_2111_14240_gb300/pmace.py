@@ -81,6 +81,10 @@ EXPORTS = ["pmace_create", "pmace_iterate", "pmace_get_image", "pmace_get_patche
            "pmace_server_release", "pmace_server_stats", "pmace_server_destroy"]
 
 
+# ABI version of include/pmace.h that the structures below mirror
+ABI_VERSION = 2
+
+
 def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
     if not os.path.exists(path):
         raise ImportError(
@@ -121,6 +125,9 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
+    if lib.pmace_abi_version() != ABI_VERSION:
+        raise ImportError(f"{path} has ABI version {lib.pmace_abi_version()}, this binding expects "
+                          f"{ABI_VERSION}: rebuild it with `python -m paper_2111_14240_gb300.build`")
     return lib
 
 

@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol(binding):
 
 
 def test_abi_version_and_status_strings(binding):
-    assert binding.pmace_abi_version() == 1
+    assert binding.pmace_abi_version() == 2
     assert binding._lib.pmace_status_string(0) == b"ok"
     assert binding._lib.pmace_status_string(4) == b"unsupported size"
 
