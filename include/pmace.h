@@ -187,6 +187,32 @@ pmace_status pmace_amplitude_energy_noalloc(const void* amps, pmace_amp_format f
                                             const float* scales, int32_t J, int32_t np,
                                             double* out, void* stream);
 
+/* ---- Data simulator (the step before the hot path) ----
+ * Measured amplitudes for a known object, made on the GPU (the forward model
+ * of Section II, z_j = |F D P_j x|^2, with the photon scaling of Section IV):
+ *   peak <= 0 : y_j = |F D P_j x| (noiseless);
+ *   peak  > 0 : y_j = sqrt(Pois(I_j peak / M_j)) * sqrt(M_j / peak), with
+ *               I_j = |F D P_j x|^2 and M_j its maximum over the window
+ *               (y_j = 0 where M_j = 0).
+ * The Poisson counts come from the counter-based generator Philox4x32-10
+ * (draw n of pixel p of window j: counter (p, j, n, 0x504d4143), key (seed
+ * low 32 bits, seed high 32 bits)) and are reproducible for a given seed.
+ *   dims, probe, offsets : as for pmace_create (kappa unused);
+ *   object  : x, n1*n2 complex;
+ *   out     : J*Np*Np float32 amplitudes in the layout pmace_create takes.
+ *   on_device : 1 = probe, object and out are device pointers (offsets host).
+ * Allocates a J*Np*Np complex scratch stack for the call and synchronises
+ * `stream`.  UNSUPPORTED_SIZE for Np outside {32, 64, 128, 256}. */
+pmace_status pmace_simulate(const pmace_dims* dims, const float* probe, const int32_t* offsets,
+                            const float* object, double peak, uint64_t seed, float* out, int on_device,
+                            void* stream);
+
+/* The photon scaling alone, on given intensities: intensity (J*Np*Np
+ * float32, >= 0) -> out (same layout), as pmace_simulate does after the
+ * forward model (peak <= 0: out = sqrt(intensity)).  Synchronises `stream`. */
+pmace_status pmace_photon_noise(const float* intensity, int32_t J, int32_t np, double peak, uint64_t seed,
+                                float* out, int on_device, void* stream);
+
 /* Select the kernel plan: agent variant `variant` (an index into the
  * per-probe-size variant table, see pmace_plan) and consensus tile height
  * tile_h in {8, 16, 32}.  Switching to a variant with another cluster size

@@ -78,7 +78,8 @@ EXPORTS = ["pmace_create", "pmace_iterate", "pmace_get_image", "pmace_get_patche
            "pmace_last_error", "pmace_status_string", "pmace_abi_version",
            "pmace_amplitude_energy_noalloc", "pmace_set_plan", "pmace_autotune",
            "pmace_server_create", "pmace_server_submit", "pmace_server_poll", "pmace_server_wait",
-           "pmace_server_release", "pmace_server_stats", "pmace_server_destroy"]
+           "pmace_server_release", "pmace_server_stats", "pmace_server_destroy",
+           "pmace_simulate", "pmace_photon_noise"]
 
 
 # ABI version of include/pmace.h that the structures below mirror
@@ -120,6 +121,9 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         "pmace_server_release": (i32, [vp, i64]),
         "pmace_server_stats": (i32, [vp, P(pmace_server_counters)]),
         "pmace_server_destroy": (None, [vp]),
+        "pmace_simulate": (i32, [P(pmace_dims), vp, vp, vp, ctypes.c_double, ctypes.c_uint64, vp,
+                                 ctypes.c_int, vp]),
+        "pmace_photon_noise": (i32, [vp, i32, i32, ctypes.c_double, ctypes.c_uint64, vp, ctypes.c_int, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -256,6 +260,36 @@ def pmace_amplitude_energy_noalloc(amps, J, np_, out, amp_format=PMACE_AMP_F32, 
     allocating nothing (see include/pmace.h)."""
     _check(_lib.pmace_amplitude_energy_noalloc(_ptr(amps), int(amp_format), _ptr(scales), int(J),
                                                int(np_), _ptr(out), _stream(stream)), None)
+
+
+def simulate(obj, probe, offsets, peak=None, seed=0, stream=None):
+    """Measured amplitudes (J, Np, Np) float32 of `obj` (n1 x n2 complex) seen
+    through `probe` at `offsets` on the GPU (include/pmace.h, pmace_simulate);
+    peak None or <= 0: noiseless.  numpy in, numpy out."""
+    obj = np.ascontiguousarray(obj, dtype=np.complex64)
+    probe = np.ascontiguousarray(probe, dtype=np.complex64)
+    offs = np.ascontiguousarray(offsets, dtype=np.int32)
+    n1, n2 = obj.shape
+    np_ = probe.shape[0]
+    out = np.empty((offs.shape[0], np_, np_), np.float32)
+    dims = pmace_dims(n1, n2, np_, offs.shape[0], 1.0)
+    _check(_lib.pmace_simulate(ctypes.byref(dims), _ptr(probe), _ptr(offs), _ptr(obj),
+                               float(peak) if peak else 0.0, int(seed) & (2**64 - 1), _ptr(out), 0,
+                               _stream(stream)), None)
+    return out
+
+
+def photon_noise(intensity, peak, seed=0, stream=None):
+    """Section IV photon scaling of float32 intensities (J, Np, Np) on the GPU
+    (include/pmace.h, pmace_photon_noise).  numpy in, numpy out."""
+    inten = np.ascontiguousarray(intensity, dtype=np.float32)
+    J, n1, n2 = inten.shape
+    if n1 != n2:
+        raise ValueError("patterns must be square")
+    out = np.empty_like(inten)
+    _check(_lib.pmace_photon_noise(_ptr(inten), int(J), int(n1), float(peak), int(seed) & (2**64 - 1),
+                                   _ptr(out), 0, _stream(stream)), None)
+    return out
 
 
 def pmace_set_plan(h, variant, tile_h, stream=None):
