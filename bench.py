@@ -452,6 +452,93 @@ def run_serve(args):
     return 0
 
 
+def run_convergence(args):
+    """Reconstruction error against iteration on the 324-window workload for
+    the alpha / kappa grid whose FP64 oracle curves are stored under
+    tests/golden (read as data; the oracle is not run here).  NRMSE as in
+    Section IV: global phase aligned, over the pixels some window covers."""
+    import glob
+    import torch
+
+    from paper_2111_14240_gb300 import build, datagen
+    from paper_2111_14240_gb300 import pmace as pm
+    build.build()
+    curves = []
+    for path in sorted(glob.glob(os.path.join(ROOT, "tests", "golden", "nrmse_p256*.json"))):
+        with open(path) as f:
+            g = json.load(f)
+        w = datagen.make_workload(g["workload"], seed=g["seed"])
+        mask = np.zeros(w.x.shape, bool)
+        for r, c in w.offsets:
+            mask[r:r + w.np_, c:c + w.np_] = True
+        x_true = w.x[mask]
+        rec = pm.Reconstruction(w.probe.astype(np.complex64), w.offsets, w.y.astype(np.float32), w.x.shape,
+                                kappa=g["kappa"])
+        pts, done, t_iter = [], 0, 0.0
+        for pt in g["points"]:
+            n = pt["iteration"] - done
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rec.iterate(n, g["alpha"], g["rho"])
+            torch.cuda.synchronize()
+            t_iter += time.perf_counter() - t0
+            done = pt["iteration"]
+            xh = rec.image().cpu().numpy().astype(np.complex128)[mask]
+            theta = np.angle(np.vdot(x_true, xh))
+            e = float(np.linalg.norm(xh - np.exp(1j * theta) * x_true) / np.linalg.norm(x_true))
+            pts.append({"iteration": done, "nrmse_gpu": e, "nrmse_oracle": pt["nrmse"]})
+        r_fp, r_data = rec.residual()
+        rec.close()
+        curves.append({"alpha": g["alpha"], "kappa": g["kappa"], "rho": g["rho"], "points": pts,
+                       "final_rel_diff": abs(pts[-1]["nrmse_gpu"] - pts[-1]["nrmse_oracle"]) / pts[-1]["nrmse_oracle"],
+                       "ms_per_iteration": 1e3 * t_iter / done, "r_fp": r_fp, "r_data": r_data})
+    best = min(curves, key=lambda c: c["points"][-1]["nrmse_gpu"])
+    print(json.dumps({"metric": "PMACE reconstruction NRMSE vs iteration (alpha / kappa sweep)",
+                      "unit": "NRMSE", "value": best["points"][-1]["nrmse_gpu"], "higher_is_better": False,
+                      "n_gpus": 1, "data": "synthetic", "dtype": "f32",
+                      "config": {"workload": WORKLOAD, "start": "energy-matched constant",
+                                 "best": {"alpha": best["alpha"], "kappa": best["kappa"]}},
+                      "curves": curves}))
+    return 0
+
+
+def run_simulate(args):
+    """Throughput of the GPU data simulator (pmace_simulate) on the p256
+    geometry, noisy (peak 1e5), inputs and output resident on the device."""
+    import torch
+
+    from paper_2111_14240_gb300 import build, datagen
+    from paper_2111_14240_gb300 import pmace as pm
+    build.build()
+    w = datagen.make_workload("p256", seed=1)
+    x = torch.from_numpy(w.x.astype(np.complex64)).cuda()
+    d = torch.from_numpy(w.probe.astype(np.complex64)).cuda()
+    out = torch.empty((w.J, w.np_, w.np_), dtype=torch.float32, device="cuda")
+    dims = pm.pmace_dims(w.x.shape[0], w.x.shape[1], w.np_, w.J, 1.0)
+    offs = np.ascontiguousarray(w.offsets, dtype=np.int32)
+
+    def once():
+        pm._check(pm._lib.pmace_simulate(pm.ctypes.byref(dims), pm._ptr(d), pm._ptr(offs), pm._ptr(x), 1e5, 7,
+                                         pm._ptr(out), 1, pm._stream(None)), None)
+
+    for _ in range(max(args.warmup, 3)):
+        once()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        once()
+    torch.cuda.synchronize()
+    s = (time.perf_counter() - t0) / args.steps
+    moved = w.J * w.np_ ** 2 * (8 + 8 + 8 + 4 + 4 + 4)   # rows write S, columns read S, intensity w/r, y
+    print(json.dumps({"metric": "PMACE simulated patterns/s", "value": w.J / s, "unit": "patterns/s",
+                      "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "ms_per_step": s * 1e3,
+                      "data": "synthetic", "dtype": "f32 (FFT), f64 (noise)",
+                      "config": {"workload": WORKLOAD, "peak": 1e5, "timed": "whole pmace_simulate call "
+                                 "(scratch allocation, three kernels, synchronisation); inputs on the device"},
+                      "bytes_per_step": moved, "GBps": moved / s / 1e9}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -467,9 +554,16 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=16)
     ap.add_argument("--serve-load", type=float, default=0.8)
     ap.add_argument("--serve-fill", type=int, default=0, help="server fill target in pixels (0: default)")
+    ap.add_argument("--convergence", action="store_true",
+                    help="reconstruction error against iteration over the stored alpha / kappa grid")
+    ap.add_argument("--simulate", action="store_true", help="time the GPU data simulator instead")
     args = ap.parse_args()
     if args.serve:
         return run_serve(args)
+    if args.convergence:
+        return run_convergence(args)
+    if args.simulate:
+        return run_simulate(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

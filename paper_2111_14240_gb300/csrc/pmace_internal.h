@@ -105,9 +105,10 @@ __host__ __device__ constexpr AgentVariant agent_variant_of(int np, int v) {
     return np == 32 ? t32[v] : np == 64 ? t64[v] : np == 128 ? t128[v] : t256[v];
 }
 // The fastest variant measured on GB300 for each probe size: the in-place
-// cross-CTA stage for 32 x 32 and 64 x 64 probes, the transposing exchange
-// (variant 4) for 128 x 128 and 256 x 256.
-__host__ __device__ constexpr int default_agent_variant(int np) { return np >= 128 ? 4 : 0; }
+// cross-CTA stage for 32 x 32 probes (variant 0) and for 64 x 64 probes
+// (variant 2: two CTAs per window, amplitudes staged in shared memory), the
+// transposing exchange (variant 4) for 128 x 128 and 256 x 256.
+__host__ __device__ constexpr int default_agent_variant(int np) { return np >= 128 ? 4 : np == 64 ? 2 : 0; }
 
 // Geometry of one agent plan (probe size, CTAs per patch).
 struct AgentPlanInfo {
