@@ -160,14 +160,13 @@ def test_nrmse_50_iterations_small():
     assert abs(eg - eo) <= TOL_NRMSE_REL * eo
 
 
-def test_f16_amplitudes_small():
-    w = datagen.make_workload("small", seed=5)
-    _check_iteration(w, 2, f16=True)
-
-
-def test_f16_amplitudes_np128():
-    w = datagen.make_workload(dict(MID128, name="mid128"), seed=6)
-    _check_iteration(w, 1, f16=True)
+@pytest.mark.parametrize("cfg,iters", [("small", 2), (dict(MID64, name="mid64"), 1),
+                                       (dict(MID128, name="mid128"), 1), ("p256", 1)],
+                         ids=["np32", "np64", "np128", "np256"])
+def test_f16_amplitudes(cfg, iters):
+    """FP16 amplitudes with a per-pattern scale, on each probe size's default plan."""
+    w = datagen.make_workload(cfg, seed=6)
+    _check_iteration(w, iters, f16=True)
 
 
 def test_deterministic_np256():
