@@ -213,6 +213,13 @@ pmace_status pmace_simulate(const pmace_dims* dims, const float* probe, const in
 pmace_status pmace_photon_noise(const float* intensity, int32_t J, int32_t np, double peak, uint64_t seed,
                                 float* out, int on_device, void* stream);
 
+/* Self-test of the bounded device-side wait of the exchange-variant agent
+ * sweep: a single CTA waits on a barrier nothing completes.  Returns
+ * PMACE_ERR_TIMEOUT when the wait gave up after its poll limit and reported
+ * it (the designed outcome; a few seconds at most), PMACE_OK if it did not
+ * (a defect), CUDA on a runtime error.  Synchronises `stream`. */
+pmace_status pmace_selftest_bounded_wait(void* stream);
+
 /* Select the kernel plan: agent variant `variant` (an index into the
  * per-probe-size variant table, see pmace_plan) and consensus tile height
  * tile_h in {8, 16, 32}.  Switching to a variant with another cluster size

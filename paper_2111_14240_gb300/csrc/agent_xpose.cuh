@@ -111,13 +111,20 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Polls of one wait before it gives up (try_wait may also suspend the
-// thread for a while on each poll).
+// A wait gives up after kXposeSpinLimit polls or kXposeWaitCycles SM
+// cycles, whichever comes first (try_wait may suspend the thread for a
+// hardware-dependent time on each poll, so the cycle bound is what caps
+// the wait at about a second).
 constexpr uint32_t kXposeSpinLimit = 1u << 22;
+constexpr long long kXposeWaitCycles = 1ll << 31;
 
 __device__ __forceinline__ void mbar_wait_bounded(uint32_t bar, uint32_t parity, int* err) {
-    for (uint32_t it = 0; it < kXposeSpinLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return;
+    const long long t0 = clock64();
+    for (uint32_t it = 1; it < kXposeSpinLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return;
+        if (clock64() - t0 > kXposeWaitCycles) break;
+    }
     if (err) atomicOr(err, 2);
 }
 

@@ -79,7 +79,7 @@ EXPORTS = ["pmace_create", "pmace_iterate", "pmace_get_image", "pmace_get_patche
            "pmace_amplitude_energy_noalloc", "pmace_set_plan", "pmace_autotune",
            "pmace_server_create", "pmace_server_submit", "pmace_server_poll", "pmace_server_wait",
            "pmace_server_release", "pmace_server_stats", "pmace_server_destroy",
-           "pmace_simulate", "pmace_photon_noise"]
+           "pmace_simulate", "pmace_photon_noise", "pmace_selftest_bounded_wait"]
 
 
 # ABI version of include/pmace.h that the structures below mirror
@@ -124,6 +124,7 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         "pmace_simulate": (i32, [P(pmace_dims), vp, vp, vp, ctypes.c_double, ctypes.c_uint64, vp,
                                  ctypes.c_int, vp]),
         "pmace_photon_noise": (i32, [vp, i32, i32, ctypes.c_double, ctypes.c_uint64, vp, ctypes.c_int, vp]),
+        "pmace_selftest_bounded_wait": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -112,3 +112,26 @@ def test_set_plan_rejects_bad_values():
     with pytest.raises(pm.PmaceError):
         rec.set_plan(0, 12)
     rec.close()
+
+
+def test_bounded_device_wait_gives_up_and_reports_timeout():
+    """The exchange variant's device-side wait, on a barrier nothing
+    completes, gives up, reports PMACE_ERR_TIMEOUT and leaves the context
+    usable (no trap, no hang)."""
+    import time
+
+    import torch
+
+    from paper_2111_14240_gb300 import pmace as pm
+    t0 = time.perf_counter()
+    st = pm._lib.pmace_selftest_bounded_wait(pm._stream(None))
+    dt = time.perf_counter() - t0
+    assert st == pm.PMACE_ERR_TIMEOUT, pm._lib.pmace_last_error(None)
+    assert dt < 30.0
+    # the context still runs work
+    w = datagen.make_workload("small", seed=46)
+    rec = _job(w)
+    rec.iterate(2, 0.5, 0.5)
+    assert np.isfinite(rec.image().cpu().numpy()).all()
+    rec.close()
+    torch.cuda.synchronize()
