@@ -128,7 +128,7 @@ __device__ __forceinline__ void mbar_wait_bounded(uint32_t bar, uint32_t parity,
     if (err) atomicOr(err, 2);
 }
 
-// Windows j0 .. jn - 1 of the job `a` on one cluster.  TMC: keep d and 1/d
+// Windows j0 .. jn - 1 of the job `a` on one cluster.  TMC: keep 1/d and v
 // in TMEM where the geometry allows (the launched kernels); the twin
 // without it only serves the occupancy query (see agent_xpose).
 template <int N, int AMP, bool TMC>
