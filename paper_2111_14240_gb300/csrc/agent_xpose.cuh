@@ -248,8 +248,26 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
                     tmem_st16(tm_addr + 32u + 16u * h, r);
                 }
             }
+            if constexpr (kTm) {
+                // d from the 1/d in TMEM: d = conj(1/d) / |1/d|^2 (0 where d is
+                // treated as absent, where the table holds 0), one approximate
+                // reciprocal per pixel instead of a load round
 #pragma unroll
-            for (int t = 0; t < r1; ++t) x[t] = cmul(__ldg(dr + b + S1 * t), x[t]);
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t r[16];
+                    tmem_ld16(tm_addr + 16u * h, r);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const float ix = __uint_as_float(r[2 * t]), iy = __uint_as_float(r[2 * t + 1]);
+                        const float m2 = fmaf(ix, ix, iy * iy);
+                        const float rm = m2 > 0.f ? __fdividef(1.0f, m2) : 0.f;
+                        x[8 * h + t] = cmul(make_float2(ix * rm, -iy * rm), x[8 * h + t]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < r1; ++t) x[t] = cmul(__ldg(dr + b + S1 * t), x[t]);
+            }
             Dft<r1, false>::run(x);
 #pragma unroll
             for (int t = 1; t < r1; ++t) x[t] = cmul(x[t], tw[b * t]);
