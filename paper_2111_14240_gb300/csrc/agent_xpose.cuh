@@ -9,10 +9,12 @@
 // Both are stored as C blocks of 16 x 16 elements; block p of A holds
 // columns [16 p, 16 p + 16) of the CTA's rows, block r of B holds rows
 // [16 r, 16 r + 16) of the CTA's columns, and inside a block element
-// (k, c) sits at k * 16 + (c ^ k), which keeps every access pattern of the
-// radix stages free of bank conflicts.  Block p of A is exactly block
-// `rank` of CTA p's B, so one 2 KB bulk copy per peer moves the row slabs
-// into the column slabs, and one per peer moves them back.
+// (k, c) sits at k * 17 + c (rows padded to 17 elements, 2176 bytes a
+// block).  Every access pattern of the radix stages is then free of bank
+// conflicts, and each address is a per-thread base plus a constant.  Block
+// p of A is exactly block `rank` of CTA p's B, so one bulk copy per peer
+// moves the row slabs into the column slabs, and one per peer moves them
+// back.
 //
 // Per window:
 //   rows   copy-in fused with the first (span Np) DIF row stage, in
@@ -49,8 +51,8 @@ struct XposeGeom {
     static constexpr int R = 16;                    // rows (and columns) per CTA
     static constexpr int C = N / R;                 // CTAs per window
     static constexpr int kThreads = N;
-    static constexpr int kBlk = R * R;              // elements per exchange block
-    static constexpr int kSlab = C * kBlk;          // elements per slab (16 N)
+    static constexpr int kBlk = R * (R + 1);        // elements per exchange block (rows padded to 17)
+    static constexpr int kSlab = C * kBlk;          // elements per slab (17 N)
     static constexpr int kBlkBytes = kBlk * (int)sizeof(float2);
     static constexpr RadixPlan kRad = radix_plan(N);
     static constexpr int r1 = kRad.first, r2 = kRad.second;
@@ -68,10 +70,12 @@ struct XposeGeom {
     static_assert(r1 * r2 == N && r2 > 1, "two radix stages per axis");
     static_assert(NB1 % kThreads == 0 && NB2 % kThreads == 0, "stages must split evenly over threads");
     static_assert(C >= 2 && C <= 16, "one block per CTA of the cluster");
+    static_assert(kBlkBytes % 16 == 0, "bulk copies move multiples of 16 bytes between 16-byte aligned blocks");
+    static_assert(S1 * r1 == N, "one twiddle table entry per (stage output, butterfly)");
 };
 
-// Slab index of element (k, c) of block blk.
-__device__ __forceinline__ int xslab(int blk, int k, int c) { return blk * 256 + k * 16 + (c ^ k); }
+// Slab index of element (k, c) of block blk (16 rows of 17 elements).
+__device__ __forceinline__ int xslab(int blk, int k, int c) { return blk * 272 + k * 17 + c; }
 // Row slab: window row k of the CTA, storage column s.
 __device__ __forceinline__ int xrow(int k, int s) { return xslab(s >> 4, k, s & 15); }
 // Column slab: storage row g, column c of the CTA.
@@ -156,7 +160,10 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
         mbar_arrive_expect_tx(bar_b, kBytes);
         mbar_arrive_expect_tx(bar_a, kBytes);
     }
-    for (int i = threadIdx.x; i < N; i += T) tw[i] = a.tw[i];
+    // twiddles of the first-stage butterflies, by stage output t then
+    // butterfly b: tw[t S1 + b] = W_N^(b t), so that the threads of a row
+    // stage read consecutive entries for each t
+    for (int i = threadIdx.x; i < N; i += T) tw[i] = a.tw[(i % S1) * (i / S1)];
     cl.sync();   // every CTA's barriers are armed before any copy can land
 
     const float two_rho_prev = 2.0f * a.rho_prev;
@@ -270,7 +277,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
             }
             Dft<r1, false>::run(x);
 #pragma unroll
-            for (int t = 1; t < r1; ++t) x[t] = cmul(x[t], tw[b * t]);
+            for (int t = 1; t < r1; ++t) x[t] = cmul(x[t], tw[t * S1 + b]);
 #pragma unroll
             for (int t = 0; t < r1; ++t) sA[xrow(k, b + S1 * t)] = x[t];
         }
@@ -327,7 +334,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
             for (int t = 0; t < r1; ++t) x[t] = sB[xcol(b + S1 * t, c)];
             Dft<r1, false>::run(x);
 #pragma unroll
-            for (int t = 1; t < r1; ++t) x[t] = cmul(x[t], tw[b * t]);
+            for (int t = 1; t < r1; ++t) x[t] = cmul(x[t], tw[t * S1 + b]);
 #pragma unroll
             for (int t = 0; t < r1; ++t) sB[xcol(b + S1 * t, c)] = x[t];
         }
@@ -357,7 +364,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
 #pragma unroll
             for (int t = 0; t < r1; ++t) x[t] = sB[xcol(b + S1 * t, c)];
 #pragma unroll
-            for (int t = 1; t < r1; ++t) x[t] = cmulc(x[t], tw[b * t]);
+            for (int t = 1; t < r1; ++t) x[t] = cmulc(x[t], tw[t * S1 + b]);
             Dft<r1, true>::run(x);
 #pragma unroll
             for (int t = 0; t < r1; ++t) sB[xcol(b + S1 * t, c)] = x[t];
@@ -396,7 +403,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
 #pragma unroll
             for (int t = 0; t < r1; ++t) x[t] = sA[xrow(k, b + S1 * t)];
 #pragma unroll
-            for (int t = 1; t < r1; ++t) x[t] = cmulc(x[t], tw[b * t]);
+            for (int t = 1; t < r1; ++t) x[t] = cmulc(x[t], tw[t * S1 + b]);
             Dft<r1, true>::run(x);
             float2* qr = a.q + wbase + (size_t)row * N;   // read (S0) and overwritten (S5) by this thread only
             float2* __restrict__ ur = a.u + wbase + (size_t)row * N;
