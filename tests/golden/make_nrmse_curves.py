@@ -9,6 +9,17 @@ the readout x_hat after every `every` iterations.  Usage:
 
 writes tests/golden/nrmse_<name>[_a<alpha>_k<kappa>].json.  Deterministic:
 the workloads come from seeded generators and the oracle is plain FP64 numpy.
+
+It also writes tests/golden/nrmse_<name>_spread_<perturbation>.json: the same
+oracle run at the bench's parameters with perturbations of the size of
+single-precision rounding, which measure how far the oracle's own error
+curve moves when nothing but rounding changes:
+
+  in32          the probe rounded to complex64 and the amplitudes to float32
+                (the inputs exactly as the GPU receives them);
+  in32_state32  the same inputs, and the carried state (the stack v and the
+                consensus stack z) rounded to complex64 after every
+                iteration, as single-precision storage would.
 """
 import json
 import os
@@ -30,25 +41,47 @@ CURVES = [("p256", 1, 100, 10, 0.5, 0.5, 1.25)] + [
     ("p256", 1, 100, 10, a, 0.5, k) for a in (0.5, 2.0, 8.0) for k in (1.25, 2.0) if (a, k) != (0.5, 1.25)]
 
 
+# (workload, seed, iterations, every, alpha, rho, kappa, perturbation): the
+# bench's parameters under rounding-sized perturbations (see above).
+SPREAD = [CURVES[0] + (p,) for p in ("in32", "in32_state32")]
+
+
 def out_name(spec):
-    name, _, _, _, alpha, _, kappa = spec
+    name, _, _, _, alpha, _, kappa = spec[:7]
+    if len(spec) == 8:
+        return f"nrmse_{name}_spread_{spec[7]}.json"
     return f"nrmse_{name}.json" if spec == CURVES[0] else f"nrmse_{name}_a{alpha:g}_k{kappa:g}.json"
 
 
-def curve(name, seed, iters, every, alpha, rho, kappa):
+def curve(name, seed, iters, every, alpha, rho, kappa, perturbation=None):
     w = datagen.make_workload(name, seed=seed)
     mask = orc.weight_image(w.probe, w.offsets, w.x.shape, kappa) > 0
+    probe, y = w.probe, w.y
+    if perturbation in ("in32", "in32_state32"):
+        probe = w.probe.astype(np.complex64).astype(np.complex128)
+        y = w.y.astype(np.float32).astype(np.float64)
+    elif perturbation is not None:
+        raise ValueError(perturbation)
+    state32 = perturbation == "in32_state32"
+    step = 1 if state32 else every
     v = z = None
     points = []
-    for k in range(every, iters + 1, every):
-        o = orc.pmace(w.y, w.probe, w.offsets, w.x.shape, alpha=alpha, rho=rho, kappa=kappa,
-                      n_iter=every, v0=v, z_prev=z)
+    for k in range(step, iters + 1, step):
+        o = orc.pmace(y, probe, w.offsets, w.x.shape, alpha=alpha, rho=rho, kappa=kappa,
+                      n_iter=step, v0=v, z_prev=z)
         v, z = o["v"], o["z"]
-        points.append(dict(iteration=k, nrmse=orc.nrmse(o["x_hat"], w.x, mask), r_fp=o["r_fp"],
-                           r_data=o["r_data"]))
-        print(name, points[-1], flush=True)
-    return dict(workload=name, seed=seed, alpha=alpha, rho=rho, kappa=kappa,
-                start="energy-matched constant", points=points)
+        if state32:
+            v = v.astype(np.complex64).astype(np.complex128)
+            z = z.astype(np.complex64).astype(np.complex128)
+        if k % every == 0:
+            points.append(dict(iteration=k, nrmse=orc.nrmse(o["x_hat"], w.x, mask), r_fp=o["r_fp"],
+                               r_data=o["r_data"]))
+            print(name, perturbation or "", points[-1], flush=True)
+    d = dict(workload=name, seed=seed, alpha=alpha, rho=rho, kappa=kappa,
+             start="energy-matched constant", points=points)
+    if perturbation is not None:
+        d["perturbation"] = perturbation
+    return d
 
 
 def write(spec):
@@ -60,6 +93,7 @@ def write(spec):
 if __name__ == "__main__":
     # independent runs, one process each; `--only-missing` skips stored curves
     import multiprocessing as mp
-    todo = [c for c in CURVES if "--only-missing" not in sys.argv or not os.path.exists(os.path.join(HERE, out_name(c)))]
+    todo = [c for c in CURVES + SPREAD
+            if "--only-missing" not in sys.argv or not os.path.exists(os.path.join(HERE, out_name(c)))]
     with mp.get_context("spawn").Pool(min(len(todo), os.cpu_count() or 1)) as pool:
         pool.map(write, todo)

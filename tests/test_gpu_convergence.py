@@ -7,6 +7,16 @@ Section IV (global phase aligned, over the pixels some window covers) of
 the GPU readout is compared with the oracle's at the same iteration counts,
 stored in tests/golden/nrmse_p256*.json by tests/golden/make_nrmse_curves.py
 (which calls only the oracle).
+
+The run at the bench's parameters does not settle within 100 iterations
+(the oracle's fixed-point residual is still near 1 there), and its error
+curve moves by a few percent under rounding alone: the FP64 oracle fed the
+inputs rounded to single precision, exactly as the GPU receives them, ends
+3 % away from the FP64-input run.  Those perturbed oracle runs are stored
+beside the curves (nrmse_p256_spread_*.json), and the bar is taken against
+them: 1 % at every iteration count before any perturbed run leaves a quarter
+of that band, and at the final count 1 % or twice the oracle's own spread,
+whichever is larger.
 """
 import glob
 import importlib.util
@@ -21,7 +31,11 @@ from paper_2111_14240_gb300 import datagen
 from tests.gpu_helpers import TOL_NRMSE_REL, rounded_inputs
 
 GOLDEN_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-CURVE_FILES = sorted(glob.glob(os.path.join(GOLDEN_DIR, "nrmse_p256*.json")))
+CURVE_FILES = [p for p in sorted(glob.glob(os.path.join(GOLDEN_DIR, "nrmse_p256*.json"))) if "_spread_" not in p]
+SPREAD_FILES = sorted(glob.glob(os.path.join(GOLDEN_DIR, "nrmse_p256_spread_*.json")))
+# Below this relative spread of the perturbed oracle runs, the oracle's error
+# at that iteration count is fixed to better than a quarter of the 1 % bar.
+TIGHT_SPREAD = TOL_NRMSE_REL / 4
 
 
 def _generator():
@@ -30,6 +44,23 @@ def _generator():
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
     return mod
+
+
+def _load(path):
+    with open(path) as f:
+        return json.load(f)
+
+
+def oracle_spread():
+    """Per stored iteration count of the bench-parameter curve, the largest
+    relative distance of a rounding-perturbed oracle run from the oracle."""
+    ref = [pt["nrmse"] for pt in _load(os.path.join(GOLDEN_DIR, "nrmse_p256.json"))["points"]]
+    spread = [0.0] * len(ref)
+    for path in SPREAD_FILES:
+        pts = [pt["nrmse"] for pt in _load(path)["points"]]
+        assert len(pts) == len(ref), path
+        spread = [max(s, abs(p - r) / r) for s, p, r in zip(spread, pts, ref)]
+    return spread
 
 
 def gpu_curve(g):
@@ -79,7 +110,15 @@ def curves():
 def test_p256_nrmse_at_bench_parameters(curves):
     g, got = next(c for c in curves if (c[0]["alpha"], c[0]["kappa"]) == (0.5, 1.25))
     ref = [pt["nrmse"] for pt in g["points"]]
-    assert abs(got[-1] - ref[-1]) <= TOL_NRMSE_REL * ref[-1]
+    spread = oracle_spread()
+    # 1 % wherever the oracle's own error is fixed to a quarter of that
+    n_tight = next((i for i, s in enumerate(spread) if s > TIGHT_SPREAD), len(spread))
+    assert n_tight >= 1, "the first stored point is already rounding-dependent"
+    for i in range(n_tight):
+        assert abs(got[i] - ref[i]) <= TOL_NRMSE_REL * ref[i], (g["points"][i]["iteration"], got[i], ref[i])
+    # the final count: 1 % or twice the oracle's rounding spread
+    bar = max(TOL_NRMSE_REL, 2.0 * spread[-1])
+    assert abs(got[-1] - ref[-1]) <= bar * ref[-1], (got[-1], ref[-1], bar)
     # the GPU run moves the error the same way over the run as the oracle's
     assert (got[-1] < got[0]) == (ref[-1] < ref[0])
 
@@ -103,12 +142,21 @@ def test_p256_alpha_kappa_sweep(curves):
 def test_golden_curves_are_the_configured_runs():
     """Every configured curve is stored and is the generator's configuration (no GPU needed)."""
     mod = _generator()
-    for spec in mod.CURVES:
+    for spec in mod.CURVES + mod.SPREAD:
         path = os.path.join(GOLDEN_DIR, mod.out_name(spec))
         assert os.path.exists(path), path
-        with open(path) as f:
-            g = json.load(f)
-        name, seed, iters, every, alpha, rho, kappa = spec
+        g = _load(path)
+        name, seed, iters, every, alpha, rho, kappa = spec[:7]
         assert (g["workload"], g["seed"], g["alpha"], g["rho"], g["kappa"]) == (name, seed, alpha, rho, kappa)
+        assert g.get("perturbation") == (spec[7] if len(spec) == 8 else None)
         assert [p["iteration"] for p in g["points"]] == list(range(every, iters + 1, every))
         assert all(np.isfinite(p["nrmse"]) and p["nrmse"] > 0 for p in g["points"])
+    assert sorted(SPREAD_FILES) == sorted(os.path.join(GOLDEN_DIR, mod.out_name(s)) for s in mod.SPREAD)
+
+
+def test_oracle_spread_is_rounding_sized():
+    """The perturbed runs start where the oracle does (they differ by rounding
+    only), and the first stored point leaves room for the 1 % bar (no GPU)."""
+    spread = oracle_spread()
+    assert spread[0] < 1e-3
+    assert spread[0] <= TIGHT_SPREAD
