@@ -19,7 +19,11 @@ curve moves when nothing but rounding changes:
                 (the inputs exactly as the GPU receives them);
   in32_state32  the same inputs, and the carried state (the stack v and the
                 consensus stack z) rounded to complex64 after every
-                iteration, as single-precision storage would.
+                iteration, as single-precision storage would;
+  in32_fft32    the same inputs, and the oracle's two transforms (fft2o,
+                ifft2o) evaluated in single precision (numpy's complex64
+                FFT), everything else in FP64: the rounding of a
+                single-precision FFT, which the GPU path also incurs.
 """
 import json
 import os
@@ -43,7 +47,15 @@ CURVES = [("p256", 1, 100, 10, 0.5, 0.5, 1.25)] + [
 
 # (workload, seed, iterations, every, alpha, rho, kappa, perturbation): the
 # bench's parameters under rounding-sized perturbations (see above).
-SPREAD = [CURVES[0] + (p,) for p in ("in32", "in32_state32")]
+SPREAD = [CURVES[0] + (p,) for p in ("in32", "in32_state32", "in32_fft32")]
+
+
+def _fft2o_32(a):
+    return np.fft.fft2(a.astype(np.complex64), norm="ortho").astype(np.complex128)
+
+
+def _ifft2o_32(a):
+    return np.fft.ifft2(a.astype(np.complex64), norm="ortho").astype(np.complex128)
 
 
 def out_name(spec):
@@ -57,11 +69,13 @@ def curve(name, seed, iters, every, alpha, rho, kappa, perturbation=None):
     w = datagen.make_workload(name, seed=seed)
     mask = orc.weight_image(w.probe, w.offsets, w.x.shape, kappa) > 0
     probe, y = w.probe, w.y
-    if perturbation in ("in32", "in32_state32"):
+    if perturbation in ("in32", "in32_state32", "in32_fft32"):
         probe = w.probe.astype(np.complex64).astype(np.complex128)
         y = w.y.astype(np.float32).astype(np.float64)
     elif perturbation is not None:
         raise ValueError(perturbation)
+    if perturbation == "in32_fft32":   # this process only (one spawned process per curve)
+        orc.fft2o, orc.ifft2o = _fft2o_32, _ifft2o_32
     state32 = perturbation == "in32_state32"
     step = 1 if state32 else every
     v = z = None
