@@ -78,7 +78,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // S3 for one spectrum coefficient A (unnormalised 2-D DFT): y A / |A|, 0
 // where A = 0; coefficients whose squared magnitude would underflow are
-// rescaled by 2^100 first.  Adds (y - |A|/Np)^2 and y^2 to the residual sums.
+// rescaled by 2^100 first.  With RES, also adds (y - |A|/Np)^2 and y^2 to
+// the residual sums; the returned value is the same either way.
+template <bool RES = true>
 __device__ __forceinline__ float2 replace_magnitude(float2 xa, float y, float inv_n, float& acc_d, float& acc_y) {
     float m2 = fmaf(xa.x, xa.x, xa.y * xa.y);
     float unscale = inv_n;
@@ -91,12 +93,14 @@ __device__ __forceinline__ float2 replace_magnitude(float2 xa, float y, float in
     float mag = 0.f;
     if (m2 > 0.f) {
         const float rs = rsqrtf(m2);
-        mag = m2 * rs * unscale;
+        if constexpr (RES) mag = m2 * rs * unscale;
         o = xa * (y * rs);
     }
-    const float e = y - mag;
-    acc_d = fmaf(e, e, acc_d);
-    acc_y = fmaf(y, y, acc_y);
+    if constexpr (RES) {
+        const float e = y - mag;
+        acc_d = fmaf(e, e, acc_d);
+        acc_y = fmaf(y, y, acc_y);
+    }
     return o;
 }
 
@@ -335,8 +339,13 @@ __device__ __forceinline__ void agent_body(const AgentArgs& a, const int j0) {
             for (int k = 0; k < R; ++k) x[k] = cp[k * RS];
             Dft<R, false>::run(x);
             const float inv_n = 1.0f / (float)N;
+            if (a.residual != 0) {
 #pragma unroll
-            for (int k = 0; k < R; ++k) x[k] = replace_magnitude(x[k], yv[k], inv_n, acc_d[p], acc_y[p]);
+                for (int k = 0; k < R; ++k) x[k] = replace_magnitude<true>(x[k], yv[k], inv_n, acc_d[p], acc_y[p]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < R; ++k) x[k] = replace_magnitude<false>(x[k], yv[k], inv_n, acc_d[p], acc_y[p]);
+            }
             Dft<R, true>::run(x);
 #pragma unroll
             for (int k = 0; k < R; ++k) cp[k * RS] = x[k];

@@ -44,6 +44,8 @@
 #include "cache_hints.cuh"
 #include "tmem.cuh"
 
+#include <type_traits>
+
 namespace pmace {
 
 template <int N>
@@ -339,22 +341,28 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
             for (int t = 0; t < r1; ++t) sB[xcol(b + S1 * t, c)] = x[t];
         }
         __syncthreads();
-        // ---- second column stage, S3, inverse second column stage
+        // ---- second column stage, S3, inverse second column stage (the
+        // data-misfit sums only on the residual iteration)
         float acc_d = 0.f, acc_y = 0.f;
+        auto column_step = [&](auto with_res) {
+            constexpr bool kRes = decltype(with_res)::value;
 #pragma unroll
-        for (int u = 0; u < U2; ++u) {
-            const int id = threadIdx.x + u * T;
-            const int c = id % 16, m = id / 16;
-            float2 x[r2];
+            for (int u = 0; u < U2; ++u) {
+                const int id = threadIdx.x + u * T;
+                const int c = id % 16, m = id / 16;
+                float2 x[r2];
 #pragma unroll
-            for (int i = 0; i < r2; ++i) x[i] = sB[xcol(m * r2 + i, c)];
-            Dft<r2, false>::run(x);
+                for (int i = 0; i < r2; ++i) x[i] = sB[xcol(m * r2 + i, c)];
+                Dft<r2, false>::run(x);
 #pragma unroll
-            for (int i = 0; i < r2; ++i) x[i] = replace_magnitude(x[i], yv[u][i], inv_n, acc_d, acc_y);
-            Dft<r2, true>::run(x);
+                for (int i = 0; i < r2; ++i) x[i] = replace_magnitude<kRes>(x[i], yv[u][i], inv_n, acc_d, acc_y);
+                Dft<r2, true>::run(x);
 #pragma unroll
-            for (int i = 0; i < r2; ++i) sB[xcol(m * r2 + i, c)] = x[i];
-        }
+                for (int i = 0; i < r2; ++i) sB[xcol(m * r2 + i, c)] = x[i];
+            }
+        };
+        if (res) column_step(std::true_type{});
+        else column_step(std::false_type{});
         __syncthreads();
         // ---- inverse first column stage (DIT, span N)
 #pragma unroll 1

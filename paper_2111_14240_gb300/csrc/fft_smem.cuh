@@ -136,9 +136,77 @@ struct Dft<8, INV> {
     __device__ __forceinline__ static void run(float2 (&x)[8]) { FourStep<4, 2, INV>::run(x); }
 };
 
+// Radix 16: the four-step split 4 x 4, with the inner twiddles folded into
+// the second radix-4 pass.  Every nontrivial W_16^m (m = j2 k1 in {1, 2, 3,
+// 6, 9}) is a real scale times a factor whose parts are +-1 or +-tan(pi/8):
+//   W^1 = c (1 - i t),  W^3 = c (t - i),  W^9 = c (-1 + i t),
+//   W^2 = r (1 - i),    W^6 = r (-1 - i),  W^4 = -i
+// (forward; F^* takes the conjugates), c = cos(pi/8), t = tan(pi/8),
+// r = 1/sqrt(2).  The factors cost two adds or two fused multiply-adds a
+// coefficient, and the scales ride on the multiply-adds of the pass that
+// follows (its inputs 1 and 3 share one scale): 144 instructions instead of
+// 160 for the plain four-step form.
 template <bool INV>
 struct Dft<16, INV> {
-    __device__ __forceinline__ static void run(float2 (&x)[16]) { FourStep<4, 4, INV>::run(x); }
+    static constexpr float kC = 0.92387953251128675613f;   // cos(pi/8)
+    static constexpr float kT = 0.41421356237309504880f;   // tan(pi/8) = sqrt(2) - 1
+    static constexpr float kR = 0.70710678118654752440f;   // 1/sqrt(2)
+    static constexpr float sg = INV ? 1.0f : -1.0f;         // sign of the twiddles' imaginary parts
+
+    // a * (p + i q) for q = sg * kT (p = 1) or p = kT (q = sg): two FMAs
+    __device__ __forceinline__ static float2 by_w1(float2 a) {   // (1 + i sg t)
+        return make_float2(fmaf(-sg * kT, a.y, a.x), fmaf(sg * kT, a.x, a.y));
+    }
+    __device__ __forceinline__ static float2 by_w3(float2 a) {   // (t + i sg)
+        return make_float2(fmaf(kT, a.x, -sg * a.y), fmaf(kT, a.y, sg * a.x));
+    }
+    __device__ __forceinline__ static float2 by_w9(float2 a) {   // (-1 - i sg t)
+        return make_float2(fmaf(sg * kT, a.y, -a.x), fmaf(-sg * kT, a.x, -a.y));
+    }
+    __device__ __forceinline__ static float2 by_w2(float2 a) {   // (1 + i sg)
+        return INV ? make_float2(a.x - a.y, a.y + a.x) : make_float2(a.x + a.y, a.y - a.x);
+    }
+    __device__ __forceinline__ static float2 by_w6(float2 a) {   // (-1 + i sg)
+        return INV ? make_float2(-a.x - a.y, a.x - a.y) : make_float2(a.y - a.x, -a.x - a.y);
+    }
+    // (-+ i) a: the radix-4 rotation
+    __device__ __forceinline__ static float2 rot(float2 a) {
+        return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+    }
+    // Radix-4 DFT of (i0, k2 * u2, k13 * u1, k13 * u3) into x[k1 + 4 k2]
+    template <int K1>
+    __device__ __forceinline__ static void pass2(float2 (&x)[16], float2 i0, float2 u1, float2 u2, float2 u3,
+                                                 float k2, float k13) {
+        const float2 a = make_float2(fmaf(k2, u2.x, i0.x), fmaf(k2, u2.y, i0.y));
+        const float2 b = make_float2(fmaf(-k2, u2.x, i0.x), fmaf(-k2, u2.y, i0.y));
+        const float2 c = u1 + u3;
+        const float2 d = rot(u1 - u3);
+        x[K1] = make_float2(fmaf(k13, c.x, a.x), fmaf(k13, c.y, a.y));
+        x[K1 + 8] = make_float2(fmaf(-k13, c.x, a.x), fmaf(-k13, c.y, a.y));
+        x[K1 + 4] = make_float2(fmaf(k13, d.x, b.x), fmaf(k13, d.y, b.y));
+        x[K1 + 12] = make_float2(fmaf(-k13, d.x, b.x), fmaf(-k13, d.y, b.y));
+    }
+    __device__ __forceinline__ static void run(float2 (&x)[16]) {
+        // first pass: t[j2][k1] = sum_j1 x[4 j1 + j2] W_4^(j1 k1)
+        float2 t[4][4];
+#pragma unroll
+        for (int j2 = 0; j2 < 4; ++j2) {
+            float2 s[4] = {x[j2], x[4 + j2], x[8 + j2], x[12 + j2]};
+            Dft<4, INV>::run(s);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) t[j2][k1] = s[k1];
+        }
+        // second pass over j2, twiddle W_16^(j2 k1) folded in
+        {
+            float2 s[4] = {t[0][0], t[1][0], t[2][0], t[3][0]};
+            Dft<4, INV>::run(s);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) x[4 * k2] = s[k2];
+        }
+        pass2<1>(x, t[0][1], by_w1(t[1][1]), by_w2(t[2][1]), by_w3(t[3][1]), kR, kC);
+        pass2<2>(x, t[0][2], by_w2(t[1][2]), rot(t[2][2]), by_w6(t[3][2]), 1.0f, kR);
+        pass2<3>(x, t[0][3], by_w3(t[1][3]), by_w6(t[2][3]), by_w9(t[3][3]), kR, kC);
+    }
 };
 
 template <bool INV>
