@@ -161,6 +161,55 @@ def pin_agent_variational(o):
         assert obj(v + dv) >= f0 - 1e-12
 
 
+def naive_idft2(a):
+    """Inverse of naive_dft2: the adjoint of the orthonormal DFT, conj(F conj(a))."""
+    return np.conj(naive_dft2(np.conj(a)))
+
+
+def pin_agent_absent_probe(o):
+    """Pixels where the probe vanishes.  D^-1 in equation F-interpolate is
+    undefined there; the reading taken is that where |d| <= 1e-30 max|d| the
+    agent returns its input at that pixel (the alpha -> infinity limit of
+    that pixel), for every alpha.  Checked against the closed form written
+    with the naive DFT:
+    (a) 1x1 windows with d = 0 return x exactly;
+    (b) an 8x8 window whose probe has exact zeros, a pixel at 0.5e-30 of the
+        peak (absent) and one at 2e-30 (present): absent pixels return x bit
+        for bit, every other pixel is (alpha x + (F^* y F D x / |F D x|) / d)
+        / (1 + alpha);
+    (c) the threshold is relative to the peak: the same probe scaled by
+        1e-40 obeys (b) with the scaled d."""
+    rng = _rng(9)
+    for alpha in (0.0, 0.5, 3.0):
+        x = complex(*rng.standard_normal(2))
+        got = o.agent(np.array([[x]]), np.array([[1.7]]), np.array([[0j]]), alpha)[0, 0]
+        assert got == x
+    n = 8
+    d = datagen.make_probe(rng, n, 2.0)
+    amax = np.abs(d).max()
+    absent = [(0, 0), (0, 5), (7, 7), (3, 6)]
+    for p in absent[:3]:
+        d[p] = 0.0
+    d[3, 6] = 0.5e-30 * amax * np.exp(0.3j)
+    d[6, 1] = 2e-30 * amax * np.exp(-1.1j)
+    assert np.abs(d).max() == amax
+    for scale in (1.0, 1e-40):
+        ds = d * scale
+        x = _crandn(rng, n, n)
+        y = np.abs(rng.standard_normal((n, n))) + 0.2
+        a = naive_dft2(ds * x)
+        back = naive_idft2(y * a / np.abs(a))
+        for alpha in (0.0, 0.7, 4.0):
+            got = o.agent(x, y, ds, alpha)
+            for i in range(n):
+                for k in range(n):
+                    if (i, k) in absent:
+                        assert got[i, k] == x[i, k], (scale, alpha, i, k)
+                    else:
+                        expect = (alpha * x[i, k] + back[i, k] / ds[i, k]) / (1.0 + alpha)
+                        assert abs(got[i, k] - expect) <= 1e-9 * abs(expect), (scale, alpha, i, k)
+
+
 # ------------------------------------------------------------------ consensus
 def pin_weight_image_bruteforce(o):
     """Lambda(p) = sum over windows containing p of |d(p - o_j)|^kappa, written

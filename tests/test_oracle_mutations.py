@@ -121,11 +121,31 @@ def _m_lambda_sqrt(o):
     o.inverse_weights = inverse_weights
 
 
+def _replace_in_source(o, old, new):
+    src = open(ORACLE_FILE).read()
+    assert old in src, old
+    exec(compile(src.replace(old, new), ORACLE_FILE, "exec"), o.__dict__)
+
+
+def _m_absent_probe_returns_zero(o):
+    _replace_in_source(o, "out = xj.astype(np.complex128).copy()", "out = np.zeros(xj.shape, dtype=np.complex128)")
+
+
+def _m_absent_probe_blended(o):
+    _replace_in_source(o, "out = xj.astype(np.complex128).copy()",
+                       "out = (alpha * xj / (1.0 + alpha)).astype(np.complex128)")
+
+
+def _m_absent_probe_absolute_threshold(o):
+    _replace_in_source(o, "ok = np.abs(probe) > TINY_PROBE * amax", "ok = np.abs(probe) > TINY_PROBE")
+
+
 MUTATIONS = [_m_probe_not_inverted, _m_alpha_swapped, _m_conj_phase, _m_unnormalised_fft,
              _m_transposed_fft, _m_no_kappa_in_numerator, _m_half_kappa_in_lambda,
              _m_transposed_offsets, _m_transposed_extract_only, _m_mann_sign,
              _m_consensus_of_w, _m_readout_of_w, _m_nrmse_theta_sign, _m_init_energy,
-             _m_lambda_sqrt]
+             _m_lambda_sqrt, _m_absent_probe_returns_zero, _m_absent_probe_blended,
+             _m_absent_probe_absolute_threshold]
 
 
 @pytest.mark.parametrize("mutate", MUTATIONS, ids=lambda f: f.__name__[3:])
