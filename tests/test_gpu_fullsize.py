@@ -39,6 +39,18 @@ def _oracle_window_after_one_iteration(w, y64, probe64, x0, j, alpha, rho, kappa
     return v0[k] + 2.0 * rho * (z - wstack[k])
 
 
+def run_boundary_samples(J, wpc, n_scan):
+    """Windows to sample: the first and last, both sides of the first cluster
+    run's end, of a run boundary near the middle and of the last run's
+    start (a cluster of the agent sweep processes wpc consecutive windows),
+    both sides of the first raster row's end, and an interior window off
+    every boundary."""
+    mid = (J // 2 // wpc) * wpc
+    last = ((J - 1) // wpc) * wpc
+    s = {0, wpc - 1, wpc, mid - 1, mid, last - 1, last, n_scan - 1, n_scan, J // 2 + 17, J - 1}
+    return sorted(j for j in s if 0 <= j < J)
+
+
 def _check(w, f16, samples, alpha=0.5, rho=0.5):
     import torch
 
@@ -56,8 +68,10 @@ def _check(w, f16, samples, alpha=0.5, rho=0.5):
     try:
         rec.iterate(1, alpha, rho)
         v = rec.patches()
-        got = {j: v[j].cpu().numpy().astype(np.complex128) for j in samples}
         plan = rec.plan()
+        if callable(samples):
+            samples = samples(w.J, plan["windows_per_cluster"])
+        got = {j: v[j].cpu().numpy().astype(np.complex128) for j in samples}
     finally:
         rec.close()
         del v
@@ -68,7 +82,7 @@ def _check(w, f16, samples, alpha=0.5, rho=0.5):
         e_w = rel_l2(got[j] * np.abs(probe64), ref * np.abs(probe64))
         e = rel_l2(got[j], ref)
         print(f"{w.name} J={w.J} f16={f16} plan={plan} window {j}: |d|v {e_w:.2e} v {e:.2e}")
-        assert e_w < TOL_ITER
+        assert e_w < TOL_ITER and e < TOL_ITER
 
 
 @pytest.fixture(scope="module")
@@ -78,13 +92,13 @@ def p128():
 
 @pytest.mark.parametrize("f16", [False, True])
 def test_p128_full_size_sampled(p128, f16):
-    J = p128.J
-    _check(p128, f16, samples=[0, 60, J // 2, J - 1])
+    n_scan = datagen.CONFIGS["p128"]["n_scan"]
+    _check(p128, f16, samples=lambda J, wpc: run_boundary_samples(J, wpc, n_scan))
 
 
 @pytest.mark.skipif(os.environ.get("PMACE_SKIP_LARGE") == "1", reason="large workload skipped on request")
 def test_large_full_size_sampled_f16():
     """8192 x 8192 object, 64009 windows of 128 x 128, FP16 amplitudes."""
     w = datagen.make_workload("large", seed=1)
-    J = w.J
-    _check(w, True, samples=[0, J // 2 + 17, J - 1])
+    n_scan = datagen.CONFIGS["large"]["n_scan"]
+    _check(w, True, samples=lambda J, wpc: run_boundary_samples(J, wpc, n_scan))

@@ -41,7 +41,11 @@ def _check_iteration(w, iters=1, alpha=0.5, rho=0.5, variant=None, f16=False, to
     e_v = rel_l2(g["v"], o["v"])
     print(f"{w.name} np={w.np_} J={w.J} plan={g['plan']} iters={iters}: "
           f"x_hat {e_img:.2e}  |d|v {e_vw:.2e}  v {e_v:.2e}")
-    assert e_img < tol and e_vw < tol
+    # the unweighted stack too: D^-1 multiplies the rounding of the
+    # single-precision transforms by 1/|d| (rms 8 for the sigma = Np / 4
+    # probes, 94 for the 256 x 256 probe with sigma 48 px), and the bar holds
+    # for it on every workload here
+    assert e_img < tol and e_vw < tol and e_v < tol
     return g, o
 
 
@@ -115,9 +119,10 @@ def _midrun_step(w, k, alpha=0.5, rho=0.5, variant=None):
     g = run_gpu(w, 1, alpha, rho, variant=variant, state=(q, xb, k, rho))
     e_img = rel_l2(g["x_hat"], o["x_hat"])
     e_vw = rel_l2(_weighted(g["v"], w.probe), _weighted(o["v"], w.probe))
+    e_v = rel_l2(g["v"], o["v"])
     print(f"{w.name} np={w.np_} mid-run k={k} plan={g['plan']}: x_hat {e_img:.2e}  |d|v {e_vw:.2e}"
-          f"  v {rel_l2(g['v'], o['v']):.2e}")
-    assert e_img < TOL_ITER and e_vw < TOL_ITER
+          f"  v {e_v:.2e}")
+    assert e_img < TOL_ITER and e_vw < TOL_ITER and e_v < TOL_ITER
     assert abs(g["r_fp"] - o["r_fp"]) < 1e-4 * o["r_fp"]
     assert abs(g["r_data"] - o["r_data"]) < 1e-4 * o["r_data"]
 
