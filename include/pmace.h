@@ -106,7 +106,12 @@ pmace_status pmace_iterate(pmace_handle h, int32_t n, const pmace_step* step, vo
 
 /* Algorithm 1's output x_hat = Lambda^-1 sum_j P_j^t |D|^kappa v_j for the
  * current v (pixels no window covers read 0).  out: n1*n2 complex, host
- * (out_on_device = 0; the call then synchronises `stream`) or device memory. */
+ * (out_on_device = 0; the call then synchronises `stream`) or device memory.
+ * With a host `out` the call also reads the job's error word after the
+ * copy: if a bounded device-side wait of an earlier agent sweep gave up, the
+ * image is still written but the call returns PMACE_ERR_TIMEOUT (the image
+ * may be wrong).  With a device `out` the call stays asynchronous and does
+ * not check; pmace_residual reports the same condition. */
 pmace_status pmace_get_image(pmace_handle h, float* out, int out_on_device, void* stream);
 
 /* The current patch stack v (J*Np*Np complex), host or device memory. */

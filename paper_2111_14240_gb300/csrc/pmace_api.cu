@@ -779,6 +779,16 @@ pmace_status pmace_create(const pmace_dims* dims, const float* probe, const int3
     PM_CREATE(cudaStreamSynchronize(s));
     PM_CREATE(cudaMemcpy(&errflag, h->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (errflag & 2) return bail_perm(fail(h, PMACE_ERR_INVALID_ARG, "init has non-finite values"));
+    // Host-side fault injection for the tests of the error paths:
+    // PMACE_INJECT_WAIT_TIMEOUT=1 marks the new job as if a bounded exchange
+    // wait of its agent sweep had given up (bit 2 of the error word); no
+    // device-side wait is involved.
+    if (const char* env = std::getenv("PMACE_INJECT_WAIT_TIMEOUT")) {
+        if (std::atoi(env) != 0) {
+            const int bit = 2;
+            PM_CREATE(cudaMemcpy(h->err, &bit, sizeof(int), cudaMemcpyHostToDevice));
+        }
+    }
 #undef PM_CREATE
     cudaFree(perm_d);
     h->iterations = 0;
@@ -932,8 +942,12 @@ pmace_status pmace_get_image(pmace_handle h, float* out, int out_on_device, void
     g.two_rho = 2.0f * h->rho_pending;
     PM_CUDA(h, launch_gather_readout(g, h->nunits, h->tile_h, s));
     if (!out_on_device) {
+        int errflag = 0;
         PM_CUDA(h, cudaMemcpyAsync(out, dst, NI * sizeof(float2), cudaMemcpyDeviceToHost, s));
+        PM_CUDA(h, cudaMemcpyAsync(&errflag, h->err, sizeof(int), cudaMemcpyDeviceToHost, s));
         PM_CUDA(h, cudaStreamSynchronize(s));
+        if (errflag & 2)
+            return fail(h, PMACE_ERR_TIMEOUT, "a bounded wait of the agent sweep's exchange gave up: the image may be wrong");
     }
     return PMACE_OK;
 }

@@ -125,3 +125,38 @@ def test_wait_times_out_without_stopping_the_job(jobs):
     res, img = srv.wait(jid)
     assert res["status"] == 0 and img is not None
     srv.close()
+
+
+def test_gave_up_wait_reaches_the_served_result_and_host_readout(jobs, monkeypatch):
+    """A job whose error word records a device-side wait that gave up is
+    retired with PMACE_ERR_TIMEOUT instead of an image, and a plain job's
+    host readout and residual report it too.  The error word is set on the
+    host at job creation (fault injection, PMACE_INJECT_WAIT_TIMEOUT); no
+    device-side wait runs out."""
+    import torch
+
+    from paper_2111_14240_gb300 import pmace as pm
+    monkeypatch.setenv("PMACE_INJECT_WAIT_TIMEOUT", "1")
+    srv = pm.Server()
+    jid = _submit(srv, pm, jobs[0])
+    res, img = srv.wait(jid)
+    srv.close()
+    assert res["done"] == 1 and res["status"] == pm.PMACE_ERR_TIMEOUT and img is None
+    j = jobs[2]
+    rec = pm.Reconstruction(j["probe"], j["w"].offsets, j["amps"], j["w"].x.shape)
+    try:
+        rec.iterate(2, j["alpha"], j["rho"])
+        rec.image()   # device readout: asynchronous, does not check
+        host = np.empty(j["w"].x.shape, np.complex64)
+        with pytest.raises(pm.PmaceError) as e:
+            pm.pmace_get_image(rec.h, host)
+        assert e.value.status == pm.PMACE_ERR_TIMEOUT
+        with pytest.raises(pm.PmaceError) as e:
+            rec.residual()
+        assert e.value.status == pm.PMACE_ERR_TIMEOUT
+        torch.cuda.synchronize()
+    finally:
+        rec.close()
+    monkeypatch.delenv("PMACE_INJECT_WAIT_TIMEOUT")
+    # a job created without the injection is unaffected
+    assert np.isfinite(_plain(pm, jobs[0])).all()
