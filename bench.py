@@ -2,12 +2,17 @@
 
 A step is one PMACE iteration (Algorithm 1) over every window of the
 workload: the fused agent sweep (steps S0-S5) and the consensus gather (S6),
-two kernel launches.  The default workload is a 600 x 600 complex object,
-a 256 x 256 probe and an 18 x 18 jittered raster (324 windows) with FP32
-amplitudes at Poisson peak 1e5, drawn by the seeded generator (synthetic
-stand-in for the paper's LANL image and probe, which are not available).
+two kernel launches.  The default workload is the largest single scan that
+fits one GPU: an 8192 x 8192 complex object, a 128 x 128 probe (Gaussian,
+sigma 32 px, random quadratic phase) and a 253 x 253 raster with a step of
+32 px and +-3 px jitter (64009 windows), FP16 amplitudes with a per-pattern
+FP32 scale at Poisson peak 1e5.  The object, probe and scan come from the
+seeded generator (a synthetic stand-in for the paper's LANL image and
+probe, which are not available); the amplitudes are made on the GPU by the
+library's simulator, outside the timed region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload large|p128|p256|small]
 
 One JSON line is printed by rank 0.  Under torchrun every rank runs an
 independent replica of the job on its own GPU (no data-path collective;
@@ -18,10 +23,13 @@ same workload.
 from __future__ import annotations
 
 import argparse
+import ctypes
+import functools
 import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -37,13 +45,31 @@ if ROOT not in sys.path:
 METRIC = "PMACE patch-updates/s"
 UNIT = "patch-updates/s"
 ALPHA, RHO, KAPPA = 0.5, 0.5, 1.25
-WORKLOAD = ("p256: object 600x600 complex64, probe 256x256 (Gaussian sigma 48 px, random quadratic "
-            "phase), 18x18 raster step 20 px +-2 px jitter = 324 windows, FP32 amplitudes, "
-            "Poisson peak 1e5, alpha 0.5, rho 0.5, kappa 1.25")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "agent_p256_traffic.json")
+
+# name -> (generator configuration, FP16 amplitudes, photon peak, description)
+WORKLOADS = {
+    "large": ("large", True, 1e5,
+              "largest single scan: object 8192x8192 complex64, probe 128x128 (Gaussian sigma 32 px, random "
+              "quadratic phase), 253x253 raster step 32 px +-3 px jitter = 64009 windows, FP16 amplitudes with "
+              "per-pattern FP32 scale, Poisson peak 1e5, alpha 0.5, rho 0.5, kappa 1.25"),
+    "p128": ("p128", True, 1e4,
+             "precision path: object 2048x2048, probe 128x128 (sigma 32 px), 121x121 raster step 16 px +-2 px = "
+             "14641 windows, FP16 amplitudes with per-pattern FP32 scale, Poisson peak 1e4, alpha 0.5, rho 0.5, "
+             "kappa 1.25"),
+    "p128_f32": ("p128", False, 1e4,
+                 "precision path with FP32 amplitudes: object 2048x2048, probe 128x128, 14641 windows, Poisson "
+                 "peak 1e4"),
+    "p256": ("p256", False, 1e5,
+             "object 600x600 complex64, probe 256x256 (Gaussian sigma 48 px, random quadratic phase), 18x18 "
+             "raster step 20 px +-2 px = 324 windows, FP32 amplitudes, Poisson peak 1e5"),
+    "small": ("small", False, 1e5,
+              "object 128x128, probe 32x32 (sigma 8 px), 13x13 raster step 8 px +-1 px = 169 windows, FP32 "
+              "amplitudes, Poisson peak 1e5"),
+}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "agent_traffic.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2111_14240_gb300", "csrc", f)
-                  for f in ("agent.cuh", "agent_xpose.cuh", "cache_hints.cuh", "tmem.cuh", "fft_smem.cuh",
-                            "pmace_internal.h")]
+                  for f in ("agent.cuh", "agent_xpose.cuh", "agent_pair.cuh", "cache_hints.cuh", "tmem.cuh",
+                            "fft_smem.cuh", "pmace_internal.h")]
 
 
 def kernel_hash() -> str:
@@ -52,6 +78,8 @@ def kernel_hash() -> str:
     import re
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
+        if not os.path.exists(p):
+            continue
         with open(p) as f:
             src = f.read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
@@ -73,63 +101,105 @@ def iteration_bytes(np_: int, J: int, n1: int, n2: int, amp_bytes: int = 4) -> i
     return J * (agent_bytes_per_patch(np_, amp_bytes) + np_ * np_ * 8) + n1 * n2 * (8 + 4)
 
 
+# ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """SM clocks and clock-event (throttle) reasons sampled every `period`
+    seconds during the timed region, by read-only NVML queries through
+    ctypes (nvidia-smi at 100 ms if NVML cannot be loaded)."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
-              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, index: int):
-        self.index = index
-        self.proc = None
-        self.lines = []
+    def __init__(self, index: int, period: float = 0.01):
+        self.index, self.period = index, period
+        self.samples = []          # (sm_mhz, max_mhz, reasons bitmask)
+        self._stop = threading.Event()
+        self._nvml = self._handle = None
+        self._proc = None
+        self.source = "none"
 
-    def __enter__(self):
+    def _open_nvml(self):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
-        except OSError:
-            self.proc = None
-        return self
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return False
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h)) != 0:
+                return False
+            self._nvml, self._handle = lib, h
+            self._reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+            return True
+        except (OSError, AttributeError):
+            return False
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+    def _sample_nvml(self):
+        sm, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        lib, h = self._nvml, self._handle
+        while not self._stop.is_set():
+            if (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(sm)) == 0
+                    and lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0
+                    and self._reasons_fn(h, ctypes.byref(rs)) == 0):
+                self.samples.append((float(sm.value), float(mx.value), int(rs.value)))
+            time.sleep(self.period)
 
-    def __exit__(self, *exc):
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-
-    def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 7:
+    def _read_smi(self):
+        names = [0x8, 0x40, 0x20, 0x4]
+        for line in self._proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 6:
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
+                bits = sum(b for b, v in zip(names, parts[2:6]) if v.lower().startswith("active"))
+                self.samples.append((float(parts[0]), float(parts[1]), bits))
             except ValueError:
                 continue
-            for n, v in zip(names, parts[3:7]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+
+    def __enter__(self):
+        if self._open_nvml():
+            self.source = f"nvml every {self.period * 1e3:.0f} ms"
+            self._thread = threading.Thread(target=self._sample_nvml, daemon=True)
+            self._thread.start()
+        else:
+            try:
+                self._proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(self.index),
+                     "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+                     "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                     "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self.source = "nvidia-smi every 100 ms"
+                self._thread = threading.Thread(target=self._read_smi, daemon=True)
+                self._thread.start()
+            except OSError:
+                self._proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        if self._proc is not None:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self._proc.kill()
+        if getattr(self, "_thread", None) is not None:
+            self._thread.join(timeout=5)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0,
+                    "source": self.source}
+        bits = 0
+        for _, _, b in self.samples:
+            bits |= b
+        return {"sm_mhz": statistics.median(s for s, _, _ in self.samples),
+                "sm_max_mhz": max(m for _, m, _ in self.samples),
+                "reasons": sorted(n for b, n in self.REASONS.items() if bits & b),
+                "samples": len(self.samples), "source": self.source}
 
 
+# ------------------------------------------------------------------ ranks
 def dist_setup():
     """One process per GPU under torchrun (RANK/LOCAL_RANK/WORLD_SIZE/MASTER_*
     from the environment).  NCCL when CUDA is available, else gloo;
@@ -175,181 +245,370 @@ def measured_peaks():
 
 
 def agent_kernel_name(plan) -> str:
-    """The agent sweep kernel a plan launches (transposing exchange or in-place cross-CTA stage)."""
-    return "agent_xpose_kernel" if plan.get("exchange") else "agent_kernel"
+    """The agent sweep kernel a plan launches."""
+    return {0: "agent_kernel", 1: "agent_xpose_kernel", 2: "agent_pair_kernel"}.get(plan.get("exchange"), "?")
 
 
-def stored_traffic():
+def stored_traffic(workload: str, J: int):
+    """DRAM bytes per launch of the agent sweep from the stored ncu counters,
+    when they were taken on the current kernel source: per window of the
+    captured case times the windows of one launch (the traffic grows with
+    the windows processed), else None."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     with open(TRAFFIC_FILE) as f:
         d = json.load(f)
-    if d.get("kernel_hash") != kernel_hash():
+    e = d.get(workload)
+    if not e or e.get("kernel_hash") != kernel_hash():
         return None
-    return float(d["bytes_per_launch"])
+    return float(e["bytes_per_window"]) * J
 
 
-# --------------------------------------------------------------------- oracle
-def oracle_rate(w, seconds: float, max_windows: int | None = None):
-    """FP64 oracle on a sub-scan of the workload: Algorithm 1 over the first
-    m windows (m sized so one iteration takes about `seconds`).  Returns
-    (patch-updates/s, m, iterations timed, seconds)."""
+def host_info():
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+        for key in ("model name", "Model", "CPU part"):
+            for line in info.splitlines():
+                if line.startswith(key):
+                    model = line.split(":", 1)[1].strip()
+                    break
+            if model:
+                break
+    except OSError:
+        pass
+    # Arm reports a part number, not a name
+    parts = {"0xd4f": "Arm Neoverse V2 (part 0xd4f)", "0xd40": "Arm Neoverse V1 (part 0xd40)",
+             "0xd0c": "Arm Neoverse N1 (part 0xd0c)", "0xd8e": "Arm Neoverse N3 (part 0xd8e)"}
+    model = parts.get(model, model)
+    return {"cpu_count": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
+
+
+# ------------------------------------------------------------------ inputs
+@functools.lru_cache(maxsize=2)
+def scan_geometry(name: str, seed: int = 1):
+    """Object, probe and scan offsets of a workload, drawn in the generator's
+    order (the amplitudes are made separately)."""
+    from paper_2111_14240_gb300 import datagen
+    c = datagen.CONFIGS[WORKLOADS[name][0]]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = datagen.make_object(rng, c["n_obj"], c["n_obj"])
+    probe = datagen.make_probe(rng, c["n_p"], c["probe_sigma"])
+    offs = datagen.make_offsets(rng, c["n_obj"], c["n_p"], c["n_scan"], c["step"], c["jitter"])
+    return x, probe, offs
+
+
+def device_inputs(name: str, seed: int = 1):
+    """A workload's inputs with the amplitudes resident on the GPU: made by
+    the library's simulator (Section II forward model, Section IV photon
+    scaling) and, for the FP16 path, stored as float16 codes y_j / s_j with
+    s_j = max y_j.  Returns (x, probe complex64, offsets, amps, scales)."""
+    import torch
+
+    from paper_2111_14240_gb300 import pmace as pm
+    cfg, f16, peak, _ = WORKLOADS[name]
+    x, probe, offs = scan_geometry(name, seed)
+    n1, n2 = x.shape
+    np_ = probe.shape[0]
+    J = offs.shape[0]
+    probe32 = np.ascontiguousarray(probe.astype(np.complex64))
+    xd = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+    dd = torch.from_numpy(probe32).cuda()
+    y = torch.empty((J, np_, np_), dtype=torch.float32, device="cuda")
+    dims = pm.pmace_dims(n1, n2, np_, J, 1.0)
+    o32 = np.ascontiguousarray(offs, dtype=np.int32)
+    pm._check(pm._lib.pmace_simulate(ctypes.byref(dims), pm._ptr(dd), pm._ptr(o32), pm._ptr(xd), float(peak),
+                                     7 + seed, pm._ptr(y), 1, pm._stream(None)), None)
+    del xd, dd
+    if not f16:
+        return x, probe32, o32, y, None
+    s = y.reshape(J, -1).amax(dim=1)
+    s = torch.where(s > 0, s, torch.ones_like(s)).contiguous()
+    codes = (y / s[:, None, None]).to(torch.float16).contiguous()
+    del y
+    torch.cuda.empty_cache()
+    return x, probe32, o32, codes, s
+
+
+def host_inputs(name: str, m: int | None = None, seed: int = 1):
+    """CPU-only inputs of the first m windows of a workload for the FP64
+    oracle: the generator's object, probe and scan, measurements of those
+    windows by the generator's float64 forward model with Poisson noise, and
+    for the FP16 path the dequantised codes (code * scale, exact in FP64).
+    The image is cut to the rows those windows cover.  Returns (y, probe,
+    offsets, shape)."""
+    from paper_2111_14240_gb300 import datagen
+    _, f16, peak, _ = WORKLOADS[name]
+    x, probe, offs = scan_geometry(name, seed)
+    offs = offs if m is None else offs[:m]
+    np_ = probe.shape[0]
+    rows = int(offs[:, 0].max()) + np_
+    x = x[:rows]
+    y = datagen.simulate(np.random.Generator(np.random.PCG64(seed + 100)), x, probe, offs, peak)
+    if f16:
+        codes, scales = datagen.quantize_amplitudes_f16(y)
+        y = datagen.dequantize_f16(codes, scales)
+    return y, probe, np.ascontiguousarray(offs), x.shape
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_baseline(name: str, seconds: float, max_windows: int, n_iter: int = 2):
+    """The FP64 oracle on the host cores, on the first m windows of the
+    workload, m sized so that n_iter iterations take about `seconds`:
+    (a) the literal single-thread Algorithm 1 (oracle/pmace_oracle.py),
+    (b) the batched variant with scipy.fft on every core
+    (oracle/pmace_batched.py).  Returns both as cpu_baseline records."""
+    from oracle import pmace_batched
     from oracle import pmace_oracle as orc
-    probe, offs, y = w.probe, w.offsets, w.y
-    # estimate the per-window cost on a few windows
-    m0 = min(8, len(offs))
+    J_full = None
+    out = {}
+    y, probe, offs, shape = host_inputs(name, m=min(16, max_windows))
     t0 = time.perf_counter()
-    orc.pmace(y[:m0], probe, offs[:m0], w.x.shape, alpha=ALPHA, rho=RHO, kappa=KAPPA, n_iter=1)
-    per = (time.perf_counter() - t0) / m0
-    m = max(1, min(len(offs), int(seconds / max(per, 1e-6))))
-    if max_windows:
-        m = min(m, max_windows)
-    t0 = time.perf_counter()
-    orc.pmace(y[:m], probe, offs[:m], w.x.shape, alpha=ALPHA, rho=RHO, kappa=KAPPA, n_iter=1)
-    dt = time.perf_counter() - t0
-    return m / dt, m, dt
+    orc.pmace(y, probe, offs, shape, alpha=ALPHA, rho=RHO, kappa=KAPPA, n_iter=1)
+    per = (time.perf_counter() - t0) / len(offs)
+    m = max(16, min(max_windows, int(seconds / n_iter / max(per, 1e-6))))
+    y, probe, offs, shape = host_inputs(name, m=m)
+    from paper_2111_14240_gb300 import datagen
+    c = datagen.CONFIGS[WORKLOADS[name][0]]
+    J_full = c["n_scan"] ** 2
+    cores = os.cpu_count() or 1
+    for kind, fn, threads in (("literal", orc.pmace, 1), ("batched", pmace_batched.pmace, cores)):
+        kw = dict(alpha=ALPHA, rho=RHO, kappa=KAPPA, n_iter=n_iter)
+        if kind == "batched":
+            kw["workers"] = cores
+        t0 = time.perf_counter()
+        fn(y, probe, offs, shape, **kw)
+        dt = time.perf_counter() - t0
+        rate = len(offs) * n_iter / dt
+        what = ("Algorithm 1 as written (oracle/pmace_oracle.py: FP64 numpy, one thread)" if kind == "literal"
+                else f"Algorithm 1 with the agents of the stack taken by scipy.fft on {cores} threads "
+                     f"(oracle/pmace_batched.py, FP64)")
+        out[kind] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                     "sample": f"{what}: {n_iter} iterations over the first {len(offs)} of {J_full} windows "
+                               f"({dt:.1f} s), the rate extrapolated to the whole scan"}
+    return out
 
 
 def run_reference(args):
     dist, world, rank, _ = dist_setup()
     if rank != 0:
         return 0
-    from paper_2111_14240_gb300 import datagen
-    w = datagen.make_workload("p256", seed=1)
-    J = w.J
+    from oracle import pmace_oracle as orc
+    name = args.workload
     budget = 150.0
     per_step = max(0.2, min(6.0, budget / max(1, args.steps + args.warmup)))
     if args.ref_seconds > 0:
         per_step = args.ref_seconds
-    from oracle import pmace_oracle as orc
-    probe, offs, y = w.probe, w.offsets, w.y
-    m0 = 8
+    y, probe, offs, shape = host_inputs(name, m=8)
     t0 = time.perf_counter()
-    orc.pmace(y[:m0], probe, offs[:m0], w.x.shape, alpha=ALPHA, rho=RHO, kappa=KAPPA, n_iter=1)
-    per = (time.perf_counter() - t0) / m0
-    m = max(1, min(J, int(per_step / per)))
-    sub = (y[:m], probe, offs[:m], w.x.shape)
+    orc.pmace(y, probe, offs, shape, alpha=ALPHA, rho=RHO, kappa=KAPPA, n_iter=1)
+    per = (time.perf_counter() - t0) / len(offs)
+    m = max(1, int(per_step / per))
+    y, probe, offs, shape = host_inputs(name, m=m)
+    m = len(offs)
     v = None
     for _ in range(args.warmup):
-        v = orc.pmace(*sub, alpha=ALPHA, rho=RHO, kappa=KAPPA, n_iter=1, v0=v)["v"]
+        v = orc.pmace(y, probe, offs, shape, alpha=ALPHA, rho=RHO, kappa=KAPPA, n_iter=1, v0=v)["v"]
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        v = orc.pmace(*sub, alpha=ALPHA, rho=RHO, kappa=KAPPA, n_iter=1, v0=v)["v"]
+        v = orc.pmace(y, probe, offs, shape, alpha=ALPHA, rho=RHO, kappa=KAPPA, n_iter=1, v0=v)["v"]
     dt = time.perf_counter() - t0
     val = m * args.steps / dt
+    from paper_2111_14240_gb300 import datagen
+    J = datagen.CONFIGS[WORKLOADS[name][0]]["n_scan"] ** 2
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "data": "synthetic", "config": {"workload": WORKLOADS[name][3]},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"Algorithm 1 (FP64 numpy, single thread) over the first {m} of "
-                                   f"{J} windows per step; each step one iteration"},
+                                   f"{J} windows per step, the rate extrapolated to the whole scan; each "
+                                   f"step one iteration"},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "host": host_info(),
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-# --------------------------------------------------------------------- ours
-def run_ours(args):
+# ------------------------------------------------------------------ ours
+def time_job(rec, steps: int, warmup: int, stream, clocks_index=None, dist=None):
+    """Warm up, then time `steps` iterations with CUDA events on the job's
+    stream (barrier + synchronize on both sides); per-kernel times from the
+    library's own event pairs.  Returns (ms, kernel times, clocks)."""
     import torch
-    dist, world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    from paper_2111_14240_gb300 import datagen
+
     from paper_2111_14240_gb300 import pmace as pm
-
-    w = datagen.make_workload("p256", seed=1)
-    J, np_ = w.J, w.np_
-    n1, n2 = w.x.shape
-    probe32 = np.ascontiguousarray(w.probe.astype(np.complex64))
-    y32 = np.ascontiguousarray(w.y.astype(np.float32))
-    stream = torch.cuda.current_stream()
-
-    rec = pm.Reconstruction(probe32, w.offsets, y32, (n1, n2), kappa=KAPPA, stream=stream)
-    plan = rec.plan()
-    rec.iterate(args.warmup, ALPHA, RHO)
+    rec.iterate(warmup, ALPHA, RHO)
     torch.cuda.synchronize()
     pm.pmace_set_profiling(rec.h, True)
     pm.pmace_kernel_times(rec.h, reset=True)
-
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
+    sampler = ClockSampler(clocks_index) if clocks_index is not None else None
+    if sampler:
+        sampler.__enter__()
+    try:
         start.record(stream)
-        rec.iterate(args.steps, ALPHA, RHO)
+        rec.iterate(steps, ALPHA, RHO)
         stop.record(stream)
         torch.cuda.synchronize()
+    finally:
+        if sampler:
+            sampler.__exit__(None, None, None)
     if dist:
         dist.barrier()
     ms = start.elapsed_time(stop)
     kt = pm.pmace_kernel_times(rec.h, reset=True)
     pm.pmace_set_profiling(rec.h, False)
+    return ms, kt, (sampler.summary() if sampler else None)
+
+
+def roofline_of(kt, J, np_, amp_bytes, workload):
+    peak, peak_kind = measured_peaks()
+    agent_avg_ms = kt["agent_ms"] / max(1, kt["agent_launches"])
+    bytes_launch = J * agent_bytes_per_patch(np_, amp_bytes)
+    achieved = bytes_launch / (agent_avg_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": stored_traffic(workload, J), "peak_kind": f"{peak_kind} copy bandwidth (burst)",
+            "algorithmic_bytes_per_launch": bytes_launch,
+            "algorithmic_bytes_per_window": agent_bytes_per_patch(np_, amp_bytes), "avg_launch_ms": agent_avg_ms}
+
+
+def extra_workload(name: str, steps: int, warmup: int, stream):
+    """Throughput and agent roofline of another workload (device-resident
+    inputs), for the record beside the headline."""
+    import torch
+
+    from paper_2111_14240_gb300 import datagen
+    from paper_2111_14240_gb300 import pmace as pm
+    cfg, f16, _, desc = WORKLOADS[name]
+    if name == "p256":
+        w = datagen.make_workload("p256", seed=1)
+        x_shape, probe32, offs = w.x.shape, w.probe.astype(np.complex64), w.offsets
+        amps, scales = torch.from_numpy(w.y.astype(np.float32)).cuda(), None
+    else:
+        x, probe32, offs, amps, scales = device_inputs(name)
+        x_shape = x.shape
+    J, np_ = len(offs), probe32.shape[0]
+    rec = pm.Reconstruction(probe32, offs, amps, x_shape, kappa=KAPPA, stream=stream,
+                            amp_format=pm.PMACE_AMP_F16_SCALED if f16 else pm.PMACE_AMP_F32, scales=scales)
+    del amps
+    ms, kt, _ = time_job(rec, steps, warmup, stream)
+    plan = rec.plan()
+    rec.close()
+    torch.cuda.empty_cache()
+    n1, n2 = x_shape
+    amp_b = 2 if f16 else 4
+    it_ms = ms / steps
+    return {"workload": desc, "value": J * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
+            "ms_per_step": it_ms, "agent_avg_ms": kt["agent_ms"] / max(1, kt["agent_launches"]),
+            "consensus_avg_ms": kt["consensus_ms"] / max(1, kt["consensus_launches"]),
+            "roofline": roofline_of(kt, J, np_, amp_b, name),
+            "iteration_frac_of_hbm": iteration_bytes(np_, J, n1, n2, amp_b) / (it_ms / 1e3) / 1e9
+            / measured_peaks()[0], "plan": plan}
+
+
+def run_ours(args):
+    import torch
+    dist, world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_2111_14240_gb300 import pmace as pm
+
+    name = args.workload
+    cfg, f16, peak, desc = WORKLOADS[name]
+    stream = torch.cuda.current_stream()
+    x, probe32, offs, amps, scales = device_inputs(name)
+    n1, n2 = x.shape
+    J, np_ = len(offs), probe32.shape[0]
+    amp_b = 2 if f16 else 4
+    fmt = pm.PMACE_AMP_F16_SCALED if f16 else pm.PMACE_AMP_F32
+
+    # host copies for the end-to-end run (pinned)
+    amps_pin = amps.cpu().pin_memory()
+    scales_pin = scales.cpu().pin_memory() if scales is not None else None
+    p_pin = torch.view_as_real(torch.from_numpy(probe32)).contiguous().pin_memory()
+
+    rec = pm.Reconstruction(probe32, offs, amps, (n1, n2), kappa=KAPPA, stream=stream, amp_format=fmt,
+                            scales=scales)
+    del amps
+    plan = rec.plan()
+    ms, kt, clocks = time_job(rec, args.steps, args.warmup, stream, clocks_index=local, dist=dist)
     r_fp, r_data = rec.residual()
     rec.close()
+    torch.cuda.empty_cache()
 
     # end to end through the C ABI from pinned host buffers: create (H2D of
-    # probe, offsets, amplitudes), K iterations, residual and image (D2H)
-    y_pin = torch.from_numpy(y32).pin_memory()
-    p_pin = torch.view_as_real(torch.from_numpy(probe32)).contiguous().pin_memory()
+    # probe, offsets, amplitudes and scales), K iterations, residual and
+    # image (D2H)
     img_pin = torch.empty((n1, n2, 2), dtype=torch.float32).pin_memory()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
-    h = pm.pmace_create(n1, n2, np_, J, KAPPA, p_pin, w.offsets, y_pin, pm.PMACE_AMP_F32,
+    h = pm.pmace_create(n1, n2, np_, J, KAPPA, p_pin, offs, amps_pin, fmt, scales=scales_pin,
                         inputs_on_device=False, stream=stream)
     pm.pmace_iterate(h, args.steps, ALPHA, RHO, stream=stream)
     pm.pmace_residual(h, stream=stream)
     pm.pmace_get_image(h, img_pin, stream=stream)
     e2e_s = time.perf_counter() - t0
     pm.pmace_destroy(h)
-    h2d = y32.nbytes + probe32.nbytes + w.offsets.nbytes
+    h2d = amps_pin.numel() * amps_pin.element_size() + probe32.nbytes + offs.nbytes + (
+        scales_pin.numel() * 4 if scales_pin is not None else 0)
     d2h = img_pin.numel() * 4 + 16
+    del amps_pin, scales_pin, img_pin
+    torch.cuda.empty_cache()
 
     ms, e2e_s = max_over_ranks(dist, [ms, e2e_s])
     if rank != 0:
         return 0
 
     value = weak_scaling_value(world, J * args.steps, ms / 1e3)
-    peak, peak_kind = measured_peaks()
-    agent_avg_ms = kt["agent_ms"] / max(1, kt["agent_launches"])
     cons_avg_ms = kt["consensus_ms"] / max(1, kt["consensus_launches"])
-    bytes_launch = J * agent_bytes_per_patch(np_)
-    achieved = bytes_launch / (agent_avg_ms / 1e3) / 1e9
-    it_bytes = iteration_bytes(np_, J, n1, n2)
+    it_bytes = iteration_bytes(np_, J, n1, n2, amp_b)
+    roof = roofline_of(kt, J, np_, amp_b, name)
+    roof["kernel"] = agent_kernel_name(plan)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "windows": J, "probe": np_, "image": [n1, n2],
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP16 amplitudes)" if f16 else "f32",
+        "data": "synthetic (seeded generator; amplitudes by the GPU simulator)",
+        "config": {"workload": desc, "windows": J, "probe": np_, "image": [n1, n2],
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "no flush: per-step working set (q, u, y) is "
-                         f"{(J * np_ * np_ * 20) / 1e6:.0f} MB > 129 MB L2",
+                         f"{(J * np_ * np_ * (16 + amp_b)) / 1e9:.2f} GB > 129 MB L2",
                    "plan": plan},
-        "roofline": {"bound": "hbm", "kernel": agent_kernel_name(plan), "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": stored_traffic(),
-                     "peak_kind": f"{peak_kind} (copy bandwidth)",
-                     "algorithmic_bytes_per_launch": bytes_launch,
-                     "avg_launch_ms": agent_avg_ms},
-        "kernels": {"agent_avg_ms": agent_avg_ms, "consensus_avg_ms": cons_avg_ms,
+        "roofline": roof,
+        "kernels": {"agent_avg_ms": roof["avg_launch_ms"], "consensus_avg_ms": cons_avg_ms,
                     "iteration_bytes": it_bytes,
-                    "iteration_GBps": it_bytes / (ms / args.steps / 1e3) / 1e9},
+                    "iteration_GBps": it_bytes / (ms / args.steps / 1e3) / 1e9,
+                    "iteration_frac_of_hbm": it_bytes / (ms / args.steps / 1e3) / 1e9 / roof["peak"]},
         "residual": {"r_fp": r_fp, "r_data": r_data},
         "gpu_launches": 2 * args.steps,
-        "clocks": clocks.summary(),
+        "clocks": clocks,
         "e2e": {"value": weak_scaling_value(world, J * args.steps, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "note": "one whole job through the C ABI from pinned host memory: create + K "
                         "iterations + residual + image readback; bytes amortised over K"},
+        "host": host_info(),
     }
+    if world == 1 and not args.no_extra:
+        line["extra"] = {}
+        for other in ("p256", "p128", "p128_f32"):
+            if other != name:
+                line["extra"][other] = extra_workload(other, args.extra_steps, args.warmup, stream)
+    if world == 1 and not args.no_serving:
+        line["serving"] = serving_record(args.serve_small_jobs, args.serve_small_pool, args.serve_load,
+                                         args.serve_fill)
     if world == 1 and not args.no_cpu_baseline:
-        rate, m, dt = oracle_rate(w, seconds=args.cpu_seconds)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"one Algorithm 1 iteration (FP64 numpy, one thread) over "
-                                          f"the first {m} of {J} windows, {dt:.1f} s"}
+        cb = oracle_baseline(name, args.cpu_seconds, args.cpu_max_windows)
+        line["cpu_baseline"] = cb["literal"]
+        line["cpu_baseline_batched"] = cb["batched"]
     print(json.dumps(line), flush=True)
     return 0
 
@@ -384,11 +643,15 @@ def serving_jobs(n_jobs: int, pool_size: int, seed: int = 7):
     return pool, jobs
 
 
-def run_serve(args):
+def serving_record(n_jobs: int, pool_size: int, load: float, fill: int = 0):
+    """The serving workload at `load` times the single-job path's capacity:
+    each job's service time alone on the plain FP32 single-job path, then
+    the same jobs through the continuous-batching server in real time with
+    Poisson arrivals.  Returns p50 / p99 job latency of both and the
+    throughput."""
     import torch
     from paper_2111_14240_gb300 import pmace as pm
-    torch.cuda.set_device(0)
-    pool, jobs = serving_jobs(args.serve_jobs, args.serve_pool)
+    pool, jobs = serving_jobs(n_jobs, pool_size)
     updates = [pool[j["p"]]["w"].J * j["iters"] for j in jobs]
     # plain FP32 single-job path: each job's service time, one at a time
     service = []
@@ -406,7 +669,7 @@ def run_serve(args):
         pm.pmace_destroy(h)
         service.append(time.perf_counter() - t0)
     total_service = sum(service)
-    rate = args.serve_load * len(jobs) / total_service          # arrivals per second
+    rate = load * len(jobs) / total_service          # arrivals per second
     gaps = [-math.log(1.0 - j["u"]) / rate for j in jobs]
     arrivals = np.cumsum(gaps)
     # FIFO one-at-a-time latencies for the same arrivals
@@ -417,7 +680,7 @@ def run_serve(args):
         lat_single.append(t - a)
     makespan_single = t
     # serving run in real time
-    srv = pm.Server(fill_pixels=args.serve_fill)
+    srv = pm.Server(fill_pixels=fill)
     ids = []
     t_start = time.perf_counter()
     for j, a in zip(jobs, arrivals):
@@ -429,31 +692,35 @@ def run_serve(args):
         ids.append(srv.submit(d["probe"], w.offsets, d["codes"], w.x.shape, j["iters"], j["alpha"], RHO,
                               amp_format=pm.PMACE_AMP_F16_SCALED, scales=d["scales"]))
     lat = []
-    last = 0.0
     for jid in ids:
         res, _ = srv.wait(jid)
         assert res["status"] == 0, res
         lat.append((res["finish_ms"] - res["submit_ms"]) / 1e3)
-        last = max(last, res["finish_ms"])
         srv.release(jid)
     makespan = time.perf_counter() - t_start
     srv.close()
     tot = float(sum(updates))
-    line = {
+    return {
         "metric": "PMACE serving job latency p50/p99 + patch-updates/s", "unit": "s",
-        "value": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-        "higher_is_better": False, "n_gpus": 1, "jobs": len(jobs), "data": "synthetic",
-        "throughput": tot / makespan, "throughput_unit": "patch-updates/s",
-        "load": args.serve_load, "arrival_rate_per_s": rate, "fill_pixels": args.serve_fill,
+        "p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+        "jobs": len(jobs), "throughput": tot / makespan, "throughput_unit": "patch-updates/s",
+        "load": load, "arrival_rate_per_s": rate, "fill_pixels": fill,
         "single_job_fp32": {"p50": float(np.percentile(lat_single, 50)),
                             "p99": float(np.percentile(lat_single, 99)),
-                            "throughput": tot / makespan_single,
-                            "sum_service_s": total_service},
-        "config": {"workload": "serving: seeded job stream, Poisson arrivals at the given fraction of the "
-                               "single-job path's capacity; object side {256,512,768,1024}, probe 64/128, "
-                               "step 8-24 px +-2, peak 1e3-1e6, 50-150 iterations, FP16 amplitudes; "
-                               f"{args.serve_pool} distinct problems shared by {len(jobs)} jobs"},
+                            "throughput": tot / makespan_single, "sum_service_s": total_service},
+        "workload": "serving: seeded job stream, Poisson arrivals at the given fraction of the single-job "
+                    "path's capacity; object side {256,512,768,1024}, probe 64/128, step 8-24 px +-2, peak "
+                    f"1e3-1e6, 50-150 iterations, FP16 amplitudes; {pool_size} distinct problems shared by "
+                    f"{len(jobs)} jobs; the single-job path runs FP32 amplitudes one job at a time (FIFO)",
     }
+
+
+def run_serve(args):
+    import torch
+    torch.cuda.set_device(0)
+    r = serving_record(args.serve_jobs, args.serve_pool, args.serve_load, args.serve_fill)
+    line = dict(r, value=r["p50"], higher_is_better=False, n_gpus=1, data="synthetic",
+                config={"workload": r.pop("workload")})
     print(json.dumps(line), flush=True)
     return 0
 
@@ -518,7 +785,7 @@ def run_convergence(args):
     print(json.dumps({"metric": "PMACE reconstruction NRMSE vs iteration (alpha / kappa sweep)",
                       "unit": "NRMSE", "value": best["points"][-1]["nrmse_gpu"], "higher_is_better": False,
                       "n_gpus": 1, "data": "synthetic", "dtype": "f32",
-                      "config": {"workload": WORKLOAD, "start": "energy-matched constant",
+                      "config": {"workload": WORKLOADS["p256"][3], "start": "energy-matched constant",
                                  "best": {"alpha": best["alpha"], "kappa": best["kappa"]}},
                       "curves": curves}))
     return 0
@@ -555,7 +822,7 @@ def run_simulate(args):
     print(json.dumps({"metric": "PMACE simulated patterns/s", "value": w.J / s, "unit": "patterns/s",
                       "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "ms_per_step": s * 1e3,
                       "data": "synthetic", "dtype": "f32 (FFT), f64 (noise)",
-                      "config": {"workload": WORKLOAD, "peak": 1e5, "timed": "whole pmace_simulate call "
+                      "config": {"workload": WORKLOADS["p256"][3], "peak": 1e5, "timed": "whole pmace_simulate call "
                                  "(scratch allocation, three kernels, synchronisation); inputs on the device"},
                       "bytes_per_step": moved, "GBps": moved / s / 1e9}))
     return 0
@@ -629,12 +896,21 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=500)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS),
+                    help="the headline workload (default: the 64009-window 8192^2 scan)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="seconds of oracle work per CPU-baseline variant")
+    ap.add_argument("--cpu-max-windows", type=int, default=4096)
     ap.add_argument("--ref-seconds", type=float, default=0.0,
                     help="reference arm: seconds of oracle work per step (0: sized for a few minutes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads' records")
+    ap.add_argument("--extra-steps", type=int, default=50)
+    ap.add_argument("--no-serving", action="store_true", help="skip the compact serving record")
+    ap.add_argument("--serve-small-jobs", type=int, default=32)
+    ap.add_argument("--serve-small-pool", type=int, default=8)
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
     ap.add_argument("--serve-jobs", type=int, default=256)
     ap.add_argument("--serve-pool", type=int, default=16)

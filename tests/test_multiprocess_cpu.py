@@ -57,7 +57,8 @@ def test_reference_arm_under_torchrun_two_ranks():
     env = dict(os.environ, PMACE_DIST_BACKEND="gloo", OMP_NUM_THREADS="1")
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
            "--master-addr=127.0.0.1", f"--master-port={_free_port()}", "bench.py", "--impl",
-           "reference", "--gpus", "2", "--steps", "1", "--warmup", "3", "--ref-seconds", "0.3"]
+           "reference", "--gpus", "2", "--steps", "1", "--warmup", "3", "--ref-seconds", "0.3",
+           "--workload", "small"]
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
