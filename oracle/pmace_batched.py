@@ -44,7 +44,8 @@ def pmace(y: np.ndarray, probe: np.ndarray, offsets: np.ndarray, shape, *, alpha
           rho: float = 0.5, kappa: float = 1.25, n_iter: int = 1, x0: np.ndarray | None = None,
           v0: np.ndarray | None = None, workers: int | None = None) -> dict:
     """Algorithm 1 from an image x0 (default: the energy-matched constant) or
-    a patch stack v0; returns the final stacks v, w, z and x_hat."""
+    a patch stack v0; returns the final stacks v, w, z, the consensus image
+    of the last step and x_hat."""
     workers = workers or os.cpu_count() or 1
     n_p = probe.shape[0]
     lam_inv = orc.inverse_weights(orc.weight_image(probe, offsets, shape, kappa))
@@ -53,9 +54,10 @@ def pmace(y: np.ndarray, probe: np.ndarray, offsets: np.ndarray, shape, *, alpha
     else:
         v = v0.astype(np.complex128).copy()
     w = z = v
+    xbar = np.zeros(shape, dtype=np.complex128)
     for _ in range(n_iter):
         w = agents_batched(v, y, probe, alpha, workers)                         # w <- F(v)
-        z = orc.redistribute(orc.consensus_image(2.0 * w - v, probe, offsets, lam_inv, kappa),
-                             offsets, n_p)                                      # z <- G(2w - v)
+        xbar = orc.consensus_image(2.0 * w - v, probe, offsets, lam_inv, kappa)
+        z = orc.redistribute(xbar, offsets, n_p)                                # z <- G(2w - v)
         v = v + 2.0 * rho * (z - w)                                             # v <- v + 2 rho (z - w)
-    return dict(v=v, w=w, z=z, x_hat=orc.readout(v, probe, offsets, lam_inv, kappa))
+    return dict(v=v, w=w, z=z, xbar=xbar, x_hat=orc.readout(v, probe, offsets, lam_inv, kappa))

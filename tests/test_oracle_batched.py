@@ -11,7 +11,7 @@ def test_batched_oracle_matches_literal_oracle():
     kw = dict(alpha=0.6, rho=0.45, kappa=1.25, n_iter=3)
     a = pmace_oracle.pmace(w.y, w.probe, w.offsets, w.x.shape, **kw)
     b = pmace_batched.pmace(w.y, w.probe, w.offsets, w.x.shape, workers=2, **kw)
-    for k in ("v", "w", "z", "x_hat"):
+    for k in ("v", "w", "z", "xbar", "x_hat"):
         assert np.linalg.norm(b[k] - a[k]) <= 1e-12 * np.linalg.norm(a[k]), k
 
 
