@@ -158,9 +158,10 @@ pmace_status pmace_kernel_times(pmace_handle h, double* agent_ms, int64_t* agent
  * staged in shared memory, how many clusters the device holds at once, how
  * the 2-D DFT is split over the cluster (exchange 0: an in-place cross-CTA
  * butterfly stage; 1: a transposing exchange of 16 x 16 blocks between the
- * Np / 16 CTAs, which then run their column transforms locally) and the
- * windows each cluster processes; for the consensus gather the image tile
- * shape. */
+ * Np / 16 CTAs, which then run their column transforms locally; 2: the same
+ * exchange with two windows per cluster at a time in packed FP32 lanes) and
+ * the windows each cluster processes; for the consensus gather the image
+ * tile shape. */
 typedef struct {
     int32_t cluster, threads, smem_bytes, tile_h, tile_w;
     int32_t variant, cols_per_thread, stage_y, max_clusters;
@@ -217,6 +218,19 @@ pmace_status pmace_simulate(const pmace_dims* dims, const float* probe, const in
  * forward model (peak <= 0: out = sqrt(intensity)).  Synchronises `stream`. */
 pmace_status pmace_photon_noise(const float* intensity, int32_t J, int32_t np, double peak, uint64_t seed,
                                 float* out, int on_device, void* stream);
+
+/* Check of the agent sweep's forward transform, a test aid: runs one
+ * iteration of Algorithm 1 exactly as pmace_iterate(h, 1, step, stream)
+ * does (the job advances by one iteration and its residuals are those of
+ * this iteration) and also writes, for every window j, the 2-D DFT of the
+ * agent's input times the probe, A_j = F (d . v_j) (Section III-A, equation
+ * F-interpolate, before the magnitude replacement), as the sweep computed
+ * it: unnormalised (np times the orthonormal F of Section II), in natural
+ * frequency order with DC at index 0.  out: J*np*np complex, device memory
+ * (its contents are overwritten, also while reordering).  Only jobs on an
+ * exchange plan (pmace_plan.exchange 1 or 2) support it; others return
+ * PMACE_ERR_UNSUPPORTED_SIZE.  Synchronises `stream`. */
+pmace_status pmace_debug_spectra(pmace_handle h, const pmace_step* step, float* out, void* stream);
 
 /* Self-test of the bounded device-side wait of the exchange-variant agent
  * sweep: a single CTA waits on a barrier nothing completes.  Returns

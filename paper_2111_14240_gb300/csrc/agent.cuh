@@ -104,6 +104,21 @@ __device__ __forceinline__ float2 replace_magnitude(float2 xa, float y, float in
     return o;
 }
 
+// Window corner j of the job, checked against the image in the PMACE_DEBUG
+// build (a corner outside [0, n1 - N] x [0, n2 - N] sets the bounds bit of
+// the error word and is clamped into range).
+template <int N>
+__device__ __forceinline__ int2 window_corner(const AgentArgs& a, int j) {
+    int2 off = a.offs[j];
+#ifdef PMACE_DEBUG
+    if (off.x < 0 || off.x > a.n1 - N || off.y < 0 || off.y > a.n2 - N) {
+        atomicOr(a.err, kErrBoundsBit);
+        off = make_int2(min(max(off.x, 0), a.n1 - N), min(max(off.y, 0), a.n2 - N));
+    }
+#endif
+    return off;
+}
+
 // S0 for one pixel: v = q + 2 rho_prev xv (closes the previous Mann step).
 __device__ __forceinline__ float2 mann_close(float2 q, float2 xv, float two_rho_prev) {
     return make_float2(fmaf(two_rho_prev, xv.x, q.x), fmaf(two_rho_prev, xv.y, q.y));
@@ -241,7 +256,7 @@ __device__ __forceinline__ void agent_body(const AgentArgs& a, const int j0) {
             for (int e = threadIdx.x; e < R * RS; e += T) tp[e] = make_float2(0.f, 0.f);
             continue;
         }
-        const int2 off = a.offs[j0 + p];
+        const int2 off = window_corner<N>(a, j0 + p);
         float2* qp = a.q + pbase_of(p);   // q in, v out: the copy-out reads v back (same thread, same pair)
         const float2* __restrict__ xb = a.xbar + (size_t)(off.x + rank * R) * a.n2 + off.y;
         for_pairs<N, R, T, BATCH>([&](int i0) {
@@ -399,7 +414,7 @@ __device__ __forceinline__ void agent_body(const AgentArgs& a, const int j0) {
         for (int p = 0; p < PPC; ++p) {
             float az = 0.f, aw = 0.f;
             if (valid(p)) {
-                const int2 off = a.offs[j0 + p];
+                const int2 off = window_corner<N>(a, j0 + p);
                 float2* qp = a.q + pbase_of(p);   // v (written by the copy-in), overwritten by q' pair by pair by one thread
                 float2* __restrict__ uo = a.u + pbase_of(p);
                 const float2* __restrict__ xb = a.xbar + (size_t)(off.x + rank * R) * a.n2 + off.y;

@@ -33,11 +33,15 @@
 // exchange, and every CTA receives a block into exactly the region whose
 // previous contents it has already sent on, so the mbarrier of the
 // receiving slab is the only synchronisation (see the ordering notes at
-// the sends).  A cluster processes a contiguous run of windows and
-// synchronises once at the start (barrier initialisation) and once at the
-// end (no CTA exits while a peer's copy may still target it).  Every wait
-// is bounded: a wait that gives up sets bit 2 of *err and the sweep runs on
-// (its results are then wrong, and the host reports PMACE_ERR_TIMEOUT).
+// the sends).  A cluster processes a contiguous run of windows; it meets
+// at the hardware cluster barrier once, after the barrier initialisation at
+// kernel start, which every CTA reaches before any data moves.  Every later
+// wait is bounded in polls and clock cycles.  A wait that gives up sets bit
+// 2 of *err (the host reports PMACE_ERR_TIMEOUT); the CTA's threads agree at
+// the next block barrier and stop: no further bulk copy is sent and the
+// remaining windows are skipped.  The end of a run is an all-to-all arrival
+// on a third mbarrier per CTA with a bounded wait: a CTA leaves only when
+// every CTA of the cluster has passed its last receive wait or stopped.
 #pragma once
 
 #include "agent.cuh"
@@ -45,6 +49,7 @@
 #include "tmem.cuh"
 
 #include <type_traits>
+
 
 namespace pmace {
 
@@ -61,14 +66,25 @@ struct XposeGeom {
     static constexpr int S1 = N / r1;               // stride of the first stage (= r2)
     static constexpr int NB1 = R * S1;              // first-stage butterflies per slab
     static constexpr int NB2 = R * r1;              // second-stage butterflies per slab
-    static constexpr int kSmem = 2 * kSlab * (int)sizeof(float2) + N * (int)sizeof(float2) + 16;
+    static constexpr int kSmem = 2 * kSlab * (int)sizeof(float2) + N * (int)sizeof(float2) + 32;
     // resident CTAs per SM: shared memory (228 KB, 1 KB reserved per CTA plus
-    // the static reduction buffer), threads, and at least 64 registers a thread
+    // the static reduction buffer), threads, and at least kRegFloor
+    // registers a thread.  For 128 x 128 windows 96 registers (5 CTAs) keep
+    // every value in registers; with 80 (6 CTAs) some spill to local memory,
+    // which missed L1 and made the sweep 4 % slower.
+    static constexpr int kRegFloor = N == 128 ? 96 : 64;
     static constexpr int kBySmem = (228 * 1024) / (kSmem + 2048);
     static constexpr int kByThreads = 2048 / kThreads;
-    static constexpr int kByRegs = 65536 / (kThreads * 64);
+    static constexpr int kByRegs = 65536 / (kThreads * kRegFloor);
     static constexpr int kMinBlocks0 = kBySmem < kByThreads ? kBySmem : kByThreads;
     static constexpr int kMinBlocks = kMinBlocks0 < kByRegs ? kMinBlocks0 : kByRegs;
+    // the dynamic shared memory a launch asks for: padded so that no more
+    // than kMinBlocks CTAs share an SM, which bounds the TMEM they allocate
+    static constexpr int kSmemLaunch0 = (228 * 1024) / (kMinBlocks + 1) - 1024 + 64;
+    static constexpr int kSmemLaunch = kSmem > kSmemLaunch0 ? kSmem : kSmemLaunch0;
+    static_assert((kMinBlocks + 1) * (kSmemLaunch + 1024) > 228 * 1024, "one more CTA must not fit an SM");
+    // (1 KB reserved per CTA, at most 320 bytes of static shared memory)
+    static_assert(kMinBlocks * (kSmemLaunch + 1024 + 320) <= 228 * 1024, "kMinBlocks CTAs must fit an SM");
     static_assert(r1 * r2 == N && r2 > 1, "two radix stages per axis");
     static_assert(NB1 % kThreads == 0 && NB2 % kThreads == 0, "stages must split evenly over threads");
     static_assert(C >= 2 && C <= 16, "one block per CTA of the cluster");
@@ -124,14 +140,47 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
 constexpr uint32_t kXposeSpinLimit = 1u << 22;
 constexpr long long kXposeWaitCycles = 1ll << 31;
 
-__device__ __forceinline__ void mbar_wait_bounded(uint32_t bar, uint32_t parity, int* err) {
-    if (mbar_try_wait(bar, parity)) return;
+// Bounded wait on an mbarrier phase; returns false (and sets bit 2 of
+// *err) when it gives up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int* err) {
+    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (uint32_t it = 1; it < kXposeSpinLimit; ++it) {
-        if (mbar_try_wait(bar, parity)) return;
+        if (mbar_try_wait(bar, parity)) return true;
         if (clock64() - t0 > kXposeWaitCycles) break;
     }
     if (err) atomicOr(err, 2);
+    return false;
+}
+// Arrive (release, cluster scope) on an mbarrier of a CTA of the cluster.
+__device__ __forceinline__ void mbar_remote_arrive(uint32_t cluster_bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+
+// The 16 amplitudes a thread of the column step needs in one window, in
+// the exchange variants' thread order (16-byte chunks, chunk k of thread t
+// at element base + (k * T + t) * chunk): FP32 values, or FP16 codes
+// converted to float (unscaled).  base: the window's first element plus
+// rank * 16 * T.
+template <int AMP, int T>
+__device__ __forceinline__ void load_amps16(const void* y, size_t base, uint64_t pol, float (&out)[16]) {
+    const uint4* p = reinterpret_cast<const uint4*>(static_cast<const char*>(y) + base * (AMP ? 2 : 4)) + threadIdx.x;
+    constexpr int NCH = AMP ? 2 : 4;
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) {
+        const uint4 v = ld_nc_l2_hint(p + (size_t)k * T, pol);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if constexpr (AMP == 1) {
+                const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[q]));
+                out[8 * k + 2 * q] = f.x;
+                out[8 * k + 2 * q + 1] = f.y;
+            } else {
+                out[4 * k + q] = __uint_as_float(w[q]);
+            }
+        }
+    }
 }
 
 // Windows j0 .. jn - 1 of the job `a` on one cluster.  TMC: keep 1/d and v
@@ -148,16 +197,17 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
     float2* sA = reinterpret_cast<float2*>(smem_raw);
     float2* sB = sA + G::kSlab;
     float2* tw = sB + G::kSlab;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(tw + N);   // [0]: B slab filled, [1]: A slab filled
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tw + N);   // [0]: B slab filled, [1]: A slab filled, [2]: run done
     __shared__ double red[(T / 32) * 4];
 
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const uint32_t a_base = smem_addr(sA), b_base = smem_addr(sB);
-    const uint32_t bar_b = smem_addr(bars), bar_a = smem_addr(bars + 1);
+    const uint32_t bar_b = smem_addr(bars), bar_a = smem_addr(bars + 1), bar_done = smem_addr(bars + 2);
     if (threadIdx.x == 0) {
         mbar_init(bar_b, 1);
         mbar_init(bar_a, 1);
+        mbar_init(bar_done, C);
         mbar_fence_init();
         mbar_arrive_expect_tx(bar_b, kBytes);
         mbar_arrive_expect_tx(bar_a, kBytes);
@@ -166,7 +216,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
     // butterfly b: tw[t S1 + b] = W_N^(b t), so that the threads of a row
     // stage read consecutive entries for each t
     for (int i = threadIdx.x; i < N; i += T) tw[i] = a.tw[(i % S1) * (i / S1)];
-    cl.sync();   // every CTA's barriers are armed before any copy can land
+    cl.sync();   // every CTA's barriers are armed before any copy or arrival can land
 
     const float two_rho_prev = 2.0f * a.rho_prev;
     const float inv_n = 1.0f / (float)N;
@@ -187,44 +237,64 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
     // TMEM, 64 columns of the thread's lane (1/d in 0..31, v in 32..63), so
     // the copy-out loads nothing from memory outside the residual iteration.
     constexpr bool kTm = TMC && G::NB1 == T && r1 == 16;
-    constexpr uint32_t kTmCols = kTm ? 64u * (uint32_t)((T / 32 + 3) / 4) : 32u;
-    static_assert(!kTm || kTmCols * G::kBySmem <= 512, "TMEM of the resident CTAs must fit an SM");
-    __shared__ uint32_t tm_sh;
-    uint32_t tm_addr = 0;
+    constexpr uint32_t kQuads = (uint32_t)((T / 32 + 3) / 4);   // warps sharing one lane quadrant
+    constexpr uint32_t kTmCols = kTm ? 64u * kQuads : 32u;
+    // the probe d itself in a second allocation of 32 columns a quadrant,
+    // where the resident CTAs' columns allow it (else d = conj(1/d) / |1/d|^2)
+    constexpr bool kTmD = kTm && (kTmCols + 32u * kQuads) * (uint32_t)G::kMinBlocks <= 512u;
+    constexpr uint32_t kTmDCols = 32u * kQuads;
+    static_assert(!kTm || kTmCols * G::kMinBlocks <= 512, "TMEM of the resident CTAs must fit an SM");
+    __shared__ uint32_t tm_sh, tm_sh_d;
+    uint32_t tm_addr = 0, tm_d = 0;
     if constexpr (kTm) {
-        if (threadIdx.x < 32) tmem_alloc(smem_addr(&tm_sh), kTmCols);
+        if (threadIdx.x < 32) {
+            if constexpr (kTmD) tmem_alloc2(smem_addr(&tm_sh), kTmCols, smem_addr(&tm_sh_d), kTmDCols);
+            else tmem_alloc(smem_addr(&tm_sh), kTmCols);
+        }
         tmem_fence_before_sync();
         __syncthreads();
         tmem_fence_after_sync();
         const int warp = threadIdx.x >> 5;
-        tm_addr = tm_sh + ((uint32_t)(32 * (warp & 3)) << 16) + 64u * (uint32_t)(warp >> 2);
+        const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+        tm_addr = tm_sh + lanes + 64u * (uint32_t)(warp >> 2);
+        if constexpr (kTmD) tm_d = tm_sh_d + lanes + 32u * (uint32_t)(warp >> 2);
         const int k = threadIdx.x / S1, b = threadIdx.x % S1;
         const float2* dr = a.dinv + (size_t)(row0 + k) * N;
+        const float2* pr = a.probe + (size_t)(row0 + k) * N;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            uint32_t r[16];
+            uint32_t r[16], p[16];
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                const float2 d = __ldg(dr + b + S1 * (8 * h + t));
-                r[2 * t] = __float_as_uint(d.x);
-                r[2 * t + 1] = __float_as_uint(d.y);
+                const float2 di = __ldg(dr + b + S1 * (8 * h + t));
+                r[2 * t] = __float_as_uint(di.x);
+                r[2 * t + 1] = __float_as_uint(di.y);
+                if constexpr (kTmD) {
+                    const float2 d = __ldg(pr + b + S1 * (8 * h + t));
+                    p[2 * t] = __float_as_uint(d.x);
+                    p[2 * t + 1] = __float_as_uint(d.y);
+                }
             }
             tmem_st16(tm_addr + 16u * h, r);
+            if constexpr (kTmD) tmem_st16(tm_d + 16u * h, p);
         }
         tmem_wait_st();
     }
 
-    // the CTA's stack rows and amplitude rows of a window (one thread each)
+    // the CTA's stack rows and amplitudes of a window (one thread each)
+    static_assert(G::NB2 / T * r2 == 16, "16 amplitudes per thread in the column step");
     auto prefetch_window = [&](int jw) {
         const size_t rb = ((size_t)jw * N + row0) * N;
         if (threadIdx.x == 0) prefetch_l2(a.q + rb, G::R * N * (uint32_t)sizeof(float2));
-        else if (threadIdx.x == T - 1) prefetch_l2(static_cast<const char*>(a.y) + rb * (AMP ? 2 : 4), G::R * N * (AMP ? 2 : 4));
+        else if (threadIdx.x == T - 1)
+            prefetch_l2(static_cast<const char*>(a.y) + ((size_t)jw * N * N + (size_t)rank * 16 * T) * (AMP ? 2 : 4),
+                        16 * T * (AMP ? 2 : 4));
     };
     prefetch_window(j0);
 
 #pragma unroll 1
     for (int j = j0; j < jn; ++j) {
-        const int2 off = a.offs[j];
+        const int2 off = window_corner<N>(a, j);
         const size_t wbase = (size_t)j * N * N;
         float yscale = 1.0f;
         if constexpr (AMP == 1) yscale = __ldg(a.yscale + j);
@@ -257,7 +327,18 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
                     tmem_st16(tm_addr + 32u + 16u * h, r);
                 }
             }
-            if constexpr (kTm) {
+            if constexpr (kTmD) {
+                // d from TMEM
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t r[16];
+                    tmem_ld16(tm_d + 16u * h, r);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t)
+                        x[8 * h + t] = cmul(make_float2(__uint_as_float(r[2 * t]), __uint_as_float(r[2 * t + 1])),
+                                            x[8 * h + t]);
+                }
+            } else if constexpr (kTm) {
                 // d from the 1/d in TMEM: d = conj(1/d) / |1/d|^2 (0 where d is
                 // treated as absent, where the table holds 0), one approximate
                 // reciprocal per pixel instead of a load round
@@ -305,24 +386,19 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
             bulk_copy_to_peer(cluster_addr(b_base + (uint32_t)rank * kBlkBytes, p), a_base + p * kBlkBytes, kBlkBytes,
                               cluster_addr(bar_b, p));
         }
-        // amplitudes of this thread's column butterflies, loaded while the exchange is in flight
+        // amplitudes of this thread's column butterflies (value u r2 + i of
+        // the thread order is element i of butterfly u), loaded while the
+        // exchange is in flight
         float yv[U2][r2];
+        {
+            float ya[16];
+            load_amps16<AMP, T>(a.y, wbase + (size_t)rank * 16 * T, pol_first, ya);
 #pragma unroll
-        for (int u = 0; u < U2; ++u) {
-            const int id = threadIdx.x + u * T;
-            const int c = id % 16, m = id / 16;
+            for (int u = 0; u < U2; ++u)
 #pragma unroll
-            for (int i = 0; i < r2; ++i) {
-                const size_t yi = wbase + (size_t)(m * r2 + i) * N + row0 + c;
-                if constexpr (AMP == 0) {
-                    yv[u][i] = ld_nc_l2_hint(static_cast<const float*>(a.y) + yi, pol_first);
-                } else {
-                    const unsigned short h = ld_nc_l2_hint(static_cast<const unsigned short*>(a.y) + yi, pol_first);
-                    yv[u][i] = __half2float(__ushort_as_half(h)) * yscale;
-                }
-            }
+                for (int i = 0; i < r2; ++i) yv[u][i] = AMP ? ya[u * r2 + i] * yscale : ya[u * r2 + i];
         }
-        mbar_wait_bounded(bar_b, parity, a.err);
+        const bool got_b = mbar_wait_bounded(bar_b, parity, a.err);
         // re-arm for the next window before this CTA's next send: every
         // peer's next A -> B copy comes after it has received that send
         if (threadIdx.x == 0 && j + 1 < jn) mbar_arrive_expect_tx(bar_b, kBytes);
@@ -340,7 +416,8 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
 #pragma unroll
             for (int t = 0; t < r1; ++t) sB[xcol(b + S1 * t, c)] = x[t];
         }
-        __syncthreads();
+        // a wait that gave up stops the CTA before it sends anything more
+        if (__syncthreads_or(!got_b)) break;
         // ---- second column stage, S3, inverse second column stage (the
         // data-misfit sums only on the residual iteration)
         float acc_d = 0.f, acc_y = 0.f;
@@ -354,6 +431,10 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
 #pragma unroll
                 for (int i = 0; i < r2; ++i) x[i] = sB[xcol(m * r2 + i, c)];
                 Dft<r2, false>::run(x);
+                if (a.spectrum) {   // check of the forward transform (kernel row m r2 + i, column row0 + c)
+#pragma unroll
+                    for (int i = 0; i < r2; ++i) a.spectrum[wbase + (size_t)(m * r2 + i) * N + row0 + c] = x[i];
+                }
 #pragma unroll
                 for (int i = 0; i < r2; ++i) x[i] = replace_magnitude<kRes>(x[i], yv[u][i], inv_n, acc_d, acc_y);
                 Dft<r2, true>::run(x);
@@ -386,7 +467,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
             bulk_copy_to_peer(cluster_addr(a_base + (uint32_t)rank * kBlkBytes, p), b_base + p * kBlkBytes, kBlkBytes,
                               cluster_addr(bar_a, p));
         }
-        mbar_wait_bounded(bar_a, parity, a.err);
+        const bool got_a = mbar_wait_bounded(bar_a, parity, a.err);
         if (threadIdx.x == 0 && j + 1 < jn) mbar_arrive_expect_tx(bar_a, kBytes);
 
         // ---- inverse second row stage (span r2)
@@ -400,7 +481,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
 #pragma unroll
             for (int i = 0; i < r2; ++i) sA[xrow(k, m * r2 + i)] = x[i];
         }
-        __syncthreads();
+        if (__syncthreads_or(!got_a)) break;
         // ---- inverse first row stage fused with S4 + S5
         float acc_z = 0.f, acc_w = 0.f;
 #pragma unroll 1
@@ -464,12 +545,24 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
         if (res) block_reduce4<T>(acc, red, a.partials + ((size_t)j * C + rank) * 4);
         parity ^= 1u;
     }
-    if constexpr (kTm) tmem_fence_before_sync();
-    cl.sync();   // every copy into this CTA has landed; no peer still reads from it
+    // End of the run: arrive on every CTA's done barrier (this CTA has passed
+    // its last receive wait, or stopped), then wait until every CTA of the
+    // cluster has.  After a full run no bulk copy into or out of this CTA is
+    // then in flight: every copy it sent was received before its receiver
+    // arrived.  The wait is bounded like the others.
+    if constexpr (kTm) {
+        tmem_wait_st();   // a stopped run may leave its last v stores outstanding
+        tmem_fence_before_sync();
+    }
+    __syncthreads();
+    if (threadIdx.x < C) mbar_remote_arrive(cluster_addr(bar_done, threadIdx.x));
+    mbar_wait_bounded(bar_done, 0, a.err);
+    __syncthreads();
     if constexpr (kTm) {
         if (threadIdx.x < 32) {
             tmem_fence_after_sync();
             tmem_dealloc(tm_sh, kTmCols);
+            if constexpr (kTmD) tmem_dealloc(tm_sh_d, kTmDCols);
         }
     }
 }
@@ -498,7 +591,7 @@ cudaLaunchConfig_t xpose_config(K, int nclusters, cudaStream_t s, cudaLaunchAttr
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nclusters * G::C), 1, 1);
     cfg.blockDim = dim3(G::kThreads, 1, 1);
-    cfg.dynamicSmemBytes = G::kSmem;
+    cfg.dynamicSmemBytes = G::kSmemLaunch;
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = G::C;
@@ -522,16 +615,16 @@ template <int N>
 cudaError_t agent_xpose(const AgentArgs* a, int amp_f16, cudaStream_t s, AgentPlanInfo* info) {
     using G = XposeGeom<N>;
     void (*fn)(const AgentArgs) = amp_f16 ? agent_xpose_kernel<N, 1> : agent_xpose_kernel<N, 0>;
-    cudaError_t e = xpose_attributes(fn, G::kSmem, G::C);
+    cudaError_t e = xpose_attributes(fn, G::kSmemLaunch, G::C);
     if (a == nullptr) {
         // The occupancy API counts a kernel that allocates TMEM as one CTA
         // per SM.  The TMEM cache takes at most 1.9 columns per KB of shared
         // memory, so 426 of an SM's 512 columns in any mix of resident CTAs,
         // and never limits residency: ask for the same kernel without it.
         void (*twin)(const AgentArgs) = agent_xpose_kernel<N, 0, false>;
-        cudaError_t et = xpose_attributes(twin, G::kSmem, G::C);
+        cudaError_t et = xpose_attributes(twin, G::kSmemLaunch, G::C);
         info->threads = G::kThreads;
-        info->smem_bytes = G::kSmem;
+        info->smem_bytes = G::kSmemLaunch;
         info->max_clusters = 0;
         if (e == cudaSuccess && et == cudaSuccess) {
             cudaLaunchAttribute attr[1];
@@ -558,7 +651,7 @@ cudaError_t agent_xpose_batched(const AgentArgs* descs, const int2* work, int nc
     if (nclusters <= 0) return cudaSuccess;
     void (*fn)(const AgentArgs*, const int2*) =
         amp_f16 ? agent_xpose_kernel_batched<N, 1> : agent_xpose_kernel_batched<N, 0>;
-    cudaError_t e = xpose_attributes(fn, G::kSmem, G::C);
+    cudaError_t e = xpose_attributes(fn, G::kSmemLaunch, G::C);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = xpose_config<N>(fn, nclusters, s, attr);

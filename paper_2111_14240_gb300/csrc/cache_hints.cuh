@@ -41,6 +41,13 @@ __device__ __forceinline__ float ld_nc_l2_hint(const float* ptr, uint64_t pol) {
     asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(ptr), "l"(pol));
     return v;
 }
+__device__ __forceinline__ uint4 ld_nc_l2_hint(const uint4* ptr, uint64_t pol) {
+    uint4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(ptr), "l"(pol));
+    return v;
+}
 __device__ __forceinline__ unsigned short ld_nc_l2_hint(const unsigned short* ptr, uint64_t pol) {
     unsigned short v;
     asm volatile("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(ptr), "l"(pol));

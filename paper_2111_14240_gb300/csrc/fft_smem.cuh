@@ -15,8 +15,23 @@
 
 namespace pmace {
 
-__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex addition and subtraction as one packed FP32 instruction (sm_100
+// and later: two lanes, each rounded exactly as the scalar instruction).
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+// a + rot(b) and a - rot(b) with rot = -i (forward) or +i (inverse), in
+// scalar form: the rotation swaps the lanes of b, which a packed
+// instruction cannot absorb.
+template <bool INV>
+__device__ __forceinline__ float2 add_rot(float2 a, float2 b) {
+    return INV ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, a.y - b.x);
+}
+template <bool INV>
+__device__ __forceinline__ float2 sub_rot(float2 a, float2 b) {
+    return INV ? make_float2(a.x + b.y, a.y - b.x) : make_float2(a.x - b.y, a.y + b.x);
+}
+// c + k a on both lanes (k real)
+__device__ __forceinline__ float2 fma_real(float k, float2 a, float2 c) { return __ffma2_rn(a, make_float2(k, k), c); }
 __device__ __forceinline__ float2 operator*(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -80,12 +95,11 @@ struct Dft<2, INV> {
 template <bool INV>
 struct Dft<4, INV> {
     __device__ __forceinline__ static void run(float2 (&x)[4]) {
-        float2 a = x[0] + x[2], b = x[0] - x[2], c = x[1] + x[3];
-        float2 d = twiddle<1, 4, INV>(x[1] - x[3]);
+        const float2 a = x[0] + x[2], b = x[0] - x[2], c = x[1] + x[3], e = x[1] - x[3];
         x[0] = a + c;
         x[2] = a - c;
-        x[1] = b + d;
-        x[3] = b - d;
+        x[1] = add_rot<INV>(b, e);   // b + W_4 e
+        x[3] = sub_rot<INV>(b, e);
     }
 };
 
@@ -131,9 +145,45 @@ struct FourStep {
     }
 };
 
+// Radix 8 as 4 x 2 (index j = 2 j1 + j2, k = k1 + 4 k2): radix-4 over j1
+// for j2 = 0, 1, the factors W_8^k1 on the odd half, radix 2 over j2.  The
+// factor 1/sqrt(2) of W_8^1 and W_8^3 rides on the fused multiply-adds of
+// the radix-2 step: W_8^1 s = r (P, -M) forward and r (M, P) inverse,
+// W_8^3 s = r (-M, -P) forward and r (-P, M) inverse, with P = s.x + s.y,
+// M = s.x - s.y.
 template <bool INV>
 struct Dft<8, INV> {
-    __device__ __forceinline__ static void run(float2 (&x)[8]) { FourStep<4, 2, INV>::run(x); }
+    __device__ __forceinline__ static void run(float2 (&x)[8]) {
+        constexpr float r = 0.70710678118654752440f;
+        float2 t[4] = {x[0], x[2], x[4], x[6]};
+        float2 s[4] = {x[1], x[3], x[5], x[7]};
+        Dft<4, INV>::run(t);
+        Dft<4, INV>::run(s);
+        x[0] = t[0] + s[0];
+        x[4] = t[0] - s[0];
+        x[2] = add_rot<INV>(t[2], s[2]);
+        x[6] = sub_rot<INV>(t[2], s[2]);
+        {
+            const float P = s[1].x + s[1].y, M = s[1].x - s[1].y;
+            if (INV) {
+                x[1] = make_float2(fmaf(M, r, t[1].x), fmaf(P, r, t[1].y));
+                x[5] = make_float2(fmaf(M, -r, t[1].x), fmaf(P, -r, t[1].y));
+            } else {
+                x[1] = make_float2(fmaf(P, r, t[1].x), fmaf(M, -r, t[1].y));
+                x[5] = make_float2(fmaf(P, -r, t[1].x), fmaf(M, r, t[1].y));
+            }
+        }
+        {
+            const float P = s[3].x + s[3].y, M = s[3].x - s[3].y;
+            if (INV) {
+                x[3] = make_float2(fmaf(P, -r, t[3].x), fmaf(M, r, t[3].y));
+                x[7] = make_float2(fmaf(P, r, t[3].x), fmaf(M, -r, t[3].y));
+            } else {
+                x[3] = make_float2(fmaf(M, -r, t[3].x), fmaf(P, -r, t[3].y));
+                x[7] = make_float2(fmaf(M, r, t[3].x), fmaf(P, r, t[3].y));
+            }
+        }
+    }
 };
 
 // Radix 16: the four-step split 4 x 4, with the inner twiddles folded into
@@ -173,18 +223,28 @@ struct Dft<16, INV> {
     __device__ __forceinline__ static float2 rot(float2 a) {
         return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
     }
-    // Radix-4 DFT of (i0, k2 * u2, k13 * u1, k13 * u3) into x[k1 + 4 k2]
-    template <int K1>
+    // Radix-4 DFT of (i0, k2 * u2, k13 * u1, k13 * u3) into x[k1 + 4 k2];
+    // ROT2: the second input is rot(u2) with k2 = 1 (u2 is passed with its
+    // lanes unswapped; the rotation goes into scalar instructions)
+    template <int K1, bool ROT2 = false>
     __device__ __forceinline__ static void pass2(float2 (&x)[16], float2 i0, float2 u1, float2 u2, float2 u3,
                                                  float k2, float k13) {
-        const float2 a = make_float2(fmaf(k2, u2.x, i0.x), fmaf(k2, u2.y, i0.y));
-        const float2 b = make_float2(fmaf(-k2, u2.x, i0.x), fmaf(-k2, u2.y, i0.y));
+        float2 a, b;
+        if constexpr (ROT2) {
+            a = add_rot<INV>(i0, u2);
+            b = sub_rot<INV>(i0, u2);
+        } else {
+            a = fma_real(k2, u2, i0);
+            b = fma_real(-k2, u2, i0);
+        }
         const float2 c = u1 + u3;
-        const float2 d = rot(u1 - u3);
-        x[K1] = make_float2(fmaf(k13, c.x, a.x), fmaf(k13, c.y, a.y));
-        x[K1 + 8] = make_float2(fmaf(-k13, c.x, a.x), fmaf(-k13, c.y, a.y));
-        x[K1 + 4] = make_float2(fmaf(k13, d.x, b.x), fmaf(k13, d.y, b.y));
-        x[K1 + 12] = make_float2(fmaf(-k13, d.x, b.x), fmaf(-k13, d.y, b.y));
+        const float2 e = u1 - u3;   // d = rot(e)
+        x[K1] = fma_real(k13, c, a);
+        x[K1 + 8] = fma_real(-k13, c, a);
+        x[K1 + 4] = INV ? make_float2(fmaf(-k13, e.y, b.x), fmaf(k13, e.x, b.y))
+                        : make_float2(fmaf(k13, e.y, b.x), fmaf(-k13, e.x, b.y));
+        x[K1 + 12] = INV ? make_float2(fmaf(k13, e.y, b.x), fmaf(-k13, e.x, b.y))
+                         : make_float2(fmaf(-k13, e.y, b.x), fmaf(k13, e.x, b.y));
     }
     __device__ __forceinline__ static void run(float2 (&x)[16]) {
         // first pass: t[j2][k1] = sum_j1 x[4 j1 + j2] W_4^(j1 k1)
@@ -204,7 +264,7 @@ struct Dft<16, INV> {
             for (int k2 = 0; k2 < 4; ++k2) x[4 * k2] = s[k2];
         }
         pass2<1>(x, t[0][1], by_w1(t[1][1]), by_w2(t[2][1]), by_w3(t[3][1]), kR, kC);
-        pass2<2>(x, t[0][2], by_w2(t[1][2]), rot(t[2][2]), by_w6(t[3][2]), 1.0f, kR);
+        pass2<2, true>(x, t[0][2], by_w2(t[1][2]), t[2][2], by_w6(t[3][2]), 1.0f, kR);
         pass2<3>(x, t[0][3], by_w3(t[1][3]), by_w6(t[2][3]), by_w9(t[3][3]), kR, kC);
     }
 };

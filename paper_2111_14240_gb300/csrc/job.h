@@ -30,6 +30,7 @@ struct pmace_job {
     int tiles_x = 0, tiles_y = 0, ntiles = 0;
     int tile_h = 16;          // gather tile height (rows), width kGatherTileW
     int nunits = 0;           // gather CTAs (tiles with long lists are split)
+    int list_len = 0;         // entries of the gather's window lists
     int gblock = 0;           // gather block length B: units split lists at multiples of B
     int nslots = 0;           // scratch slots of split tiles
 

@@ -146,20 +146,59 @@ std::vector<int> amp_row_order(int np, int variant) {
     return perm;
 }
 
+// Layout of one window's stored amplitudes for an agent variant: for every
+// stored position, the natural index (frequency row * np + frequency
+// column) of the amplitude held there.  The in-place cross-CTA variants
+// store kernel rows (amp_row_order) of kernel columns (the DIF order of the
+// row stages), row-major.  The exchange variants store each thread's values
+// contiguously ("thread order"): CTA `rank` of the window's cluster reads
+// the 16 amplitudes of its column-step butterflies as 16-byte chunks, chunk
+// k of thread t at ((rank * chunks + k) * threads + t) * 16 bytes, so a warp
+// loads 512 contiguous bytes per instruction.  Value f of a thread (f = u r2
+// + i: butterfly u of the thread, element i) sits at kernel row
+// m r2 + i, column 16 rank + c, with m = (t + u threads) / 16 and
+// c = (t + u threads) % 16 (the column step's own indexing).
+std::vector<int> amp_layout(int np, int variant, int elem) {
+    const AgentVariant v = agent_variant_of(np, variant);
+    const std::vector<int> rows = amp_row_order(np, variant);
+    std::vector<int> cols;
+    dif_order(radices_of(np), 0, np, cols);
+    std::vector<int> out((size_t)np * np);
+    if (!v.exchange) {
+        for (int g = 0; g < np; ++g)
+            for (int c = 0; c < np; ++c) out[(size_t)g * np + c] = rows[g] * np + cols[c];
+        return out;
+    }
+    const RadixPlan rp = radix_plan(np);
+    const int T = np, C = np / 16, U2 = 16 * rp.first / T, F = U2 * rp.second, CH = 16 / elem, NCH = F / CH;
+    for (int rank = 0; rank < C; ++rank)
+        for (int k = 0; k < NCH; ++k)
+            for (int t = 0; t < T; ++t)
+                for (int e = 0; e < CH; ++e) {
+                    const int f = k * CH + e, u = f / rp.second, i = f % rp.second;
+                    const int id = t + u * T, m = id / 16, c = id % 16;
+                    const int g = m * rp.second + i, col = 16 * rank + c;
+                    out[(((size_t)rank * NCH + k) * T + t) * CH + e] = rows[g] * np + cols[col];
+                }
+    return out;
+}
+
 // Windows each agent cluster processes: the variant's own count, or for the
 // transposing exchange (a run of windows per cluster) J spread over four
 // times the clusters the device holds at once, and at most 8: short runs let
 // the clusters that finish early take up the remaining ones, which balances
 // SMs that hold different numbers of CTAs (PMACE_AGENT_WPC fixes the run).
+// The packed-lane sweep counts in pairs of windows, so its runs are even.
 int windows_per_cluster(int np, int variant, int J, const AgentPlanInfo& info) {
     const AgentVariant v = agent_variant_of(np, variant);
     if (!v.exchange) return v.windows;
-    if (const char* env = std::getenv("PMACE_AGENT_WPC")) {   // fixed run length
+    const int unit = v.exchange == 2 ? 2 : 1;   // the packed-lane sweep takes windows in pairs
+    if (const char* env = std::getenv("PMACE_AGENT_WPC")) {   // fixed run length (rounded up to the unit)
         const int w = std::atoi(env);
-        if (w > 0) return w;
+        if (w > 0) return (w + unit - 1) / unit * unit;
     }
-    const int m = 4 * std::max(info.max_clusters, 1);
-    return std::max(1, std::min(8, (J + m - 1) / m));
+    const int m = 4 * std::max(info.max_clusters, 1) * unit;
+    return unit * std::max(1, std::min(8 / unit, (J + m - 1) / m));
 }
 
 // Gather tables of one tile height: for every tile_h x kGatherTileW image
@@ -326,6 +365,7 @@ pmace_status install_gather_tables(pmace_job* h, int tile_h, cudaStream_t s) {
     h->bytes += bytes - h->gather_bytes;
     h->gather_bytes = bytes;
     h->tile_list = list;
+    h->list_len = (int)t.list.size();
     h->units = units;
     h->tile_seg = seg;
     h->gscratch = scratch;
@@ -366,12 +406,9 @@ pmace_status build_tables(pmace_job* h, const std::vector<float>& probe_h,
         const double ang = -2.0 * M_PI * (double)m / (double)np;
         tw[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
-    // row and column spectrum orders of the agent kernel: the two in-place
-    // row stages leave each row digit-reversed; along columns, local row k2
-    // of CTA `rank` holds frequency rank + cluster * k2 after the cross-CTA
-    // stage and the in-register column DFT
-    std::vector<int> rowperm, colperm = amp_row_order(np, h->variant);
-    dif_order(radices_of(np), 0, np, rowperm);
+    // where the agent kernel reads each amplitude (spectrum orders of its
+    // stages, and for the exchange variants the thread order)
+    const std::vector<int> layout = amp_layout(np, h->variant, h->amp_f16 ? 2 : 4);
 
     PM_CUDA(h, dalloc(h, &h->probe, P));
     PM_CUDA(h, dalloc(h, &h->dinv, P));
@@ -387,11 +424,9 @@ pmace_status build_tables(pmace_job* h, const std::vector<float>& probe_h,
     PM_CUDA(h, up(h->tw, tw.data(), np * sizeof(float2)));
     PM_CUDA(h, up(h->wk, wk.data(), P * sizeof(float)));
     PM_CUDA(h, up(h->offs, offs_h.data(), (size_t)J * 2 * sizeof(int32_t)));
-    // permutation tables (row order, then column order) live only until the amplitude pass
-    PM_CUDA(h, cudaMalloc(perm_out, 2 * np * sizeof(int)));
-    std::vector<int> both(rowperm);
-    both.insert(both.end(), colperm.begin(), colperm.end());
-    PM_CUDA(h, up(*perm_out, both.data(), both.size() * sizeof(int)));
+    // the layout table lives only until the amplitude pass
+    PM_CUDA(h, cudaMalloc(perm_out, P * sizeof(int)));
+    PM_CUDA(h, up(*perm_out, layout.data(), P * sizeof(int)));
     return PMACE_OK;
 }
 
@@ -451,6 +486,11 @@ GatherArgs gather_args(const pmace_job* h) {
     g.n2 = h->dims.n2;
     g.np = h->dims.np;
     g.tiles_x = h->tiles_x;
+    g.J = h->dims.J;
+    g.list_len = h->list_len;
+    g.ntiles = h->ntiles;
+    g.nslots = h->nslots;
+    g.err = h->err;
     return g;
 }
 
@@ -467,6 +507,7 @@ AgentArgs agent_args(const pmace_job* h, float alpha, float rho) {
     a.offs = h->offs;
     a.partials = h->partials;
     a.n2 = h->dims.n2;
+    a.n1 = h->dims.n1;
     a.J = h->dims.J;
     a.alpha = alpha;
     a.rho_cur = rho;
@@ -485,9 +526,11 @@ namespace {
 
 // One iteration of Algorithm 1: agent sweep (S0-S5) then consensus (S6);
 // `residual`: the sweep also writes the residual partial sums.
-pmace_status launch_iteration(pmace_job* h, float alpha, float rho, cudaStream_t s, bool events, bool residual) {
+pmace_status launch_iteration(pmace_job* h, float alpha, float rho, cudaStream_t s, bool events, bool residual,
+                              float2* spectrum = nullptr) {
     AgentArgs a = agent_args(h, alpha, rho);
     a.residual = residual ? 1 : 0;
+    a.spectrum = spectrum;
     GatherArgs g = gather_args(h);
     g.src = h->u;
     g.out = h->xbar;
@@ -541,9 +584,9 @@ pmace_status ensure_graph(pmace_job* h, float alpha, float rho) {
     return PMACE_OK;
 }
 
-// Switch the agent variant and the gather tile height.  A different cluster
-// size changes the row order the amplitudes are stored in, so they are
-// re-laid out on the device (through u, which is dead between iterations).
+// Switch the agent variant and the gather tile height.  A variant with
+// another amplitude layout (amp_layout) has them re-laid out on the device
+// (through u, which is dead between iterations).
 pmace_status switch_plan(pmace_job* h, int variant, int tile_h, cudaStream_t s) {
     const int np = h->dims.np, J = h->dims.J;
     if (variant < 0 || variant >= kAgentVariants)
@@ -557,17 +600,19 @@ pmace_status switch_plan(pmace_job* h, int variant, int tile_h, cudaStream_t s) 
             return fail(h, PMACE_ERR_UNSUPPORTED_SIZE, "agent variant %d cannot run on this device", variant);
         }
         const int c_new = agent_variant_of(np, variant).cluster;
-        const std::vector<int> o_old = amp_row_order(np, h->variant), o_new = amp_row_order(np, variant);
-        if (o_old != o_new) {
-            std::vector<int> inv(np), map(np);
-            for (int g = 0; g < np; ++g) inv[o_old[g]] = g;
-            for (int g = 0; g < np; ++g) map[g] = inv[o_new[g]];   // new row g <- old row map[g]
+        const int elem = h->amp_f16 ? 2 : 4;
+        const std::vector<int> l_old = amp_layout(np, h->variant, elem), l_new = amp_layout(np, variant, elem);
+        if (l_old != l_new) {
+            const size_t P = (size_t)np * np;
+            std::vector<int> inv(P), map(P);
+            for (size_t e = 0; e < P; ++e) inv[l_old[e]] = (int)e;
+            for (size_t e = 0; e < P; ++e) map[e] = inv[l_new[e]];   // new position e <- old position map[e]
             int* map_d = nullptr;
-            PM_CUDA(h, cudaMalloc(&map_d, np * sizeof(int)));
-            const size_t ybytes = (size_t)J * np * np * (h->amp_f16 ? 2 : 4);
-            cudaError_t e = cudaMemcpyAsync(map_d, map.data(), np * sizeof(int), cudaMemcpyHostToDevice, s);
+            PM_CUDA(h, cudaMalloc(&map_d, P * sizeof(int)));
+            const size_t ybytes = (size_t)J * P * elem;
+            cudaError_t e = cudaMemcpyAsync(map_d, map.data(), P * sizeof(int), cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess) e = cudaMemcpyAsync(h->u, h->y, ybytes, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess) e = launch_relayout_rows(h->y, h->u, map_d, J, np, h->amp_f16 ? 2 : 4, s);
+            if (e == cudaSuccess) e = launch_relayout_window(h->y, h->u, map_d, J, np, elem, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             cudaFree(map_d);
             if (e != cudaSuccess) return cuda_fail(h, e, "amplitude re-layout");
@@ -745,7 +790,7 @@ pmace_status pmace_create(const pmace_dims* dims, const float* probe, const int3
                                   inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     }
     double* sum_partials = h->partials + (size_t)J * kMaxCluster * 4;
-    PM_CREATE(launch_prep_amps(amps_dev, h->amp_f16, h->yscale, h->y, perm_d, perm_d + np, J, np,
+    PM_CREATE(launch_prep_amps(amps_dev, h->amp_f16, h->yscale, h->y, perm_d, J, np,
                                sum_partials, h->err, kPrepBlocks, s));
     PM_CREATE(launch_reduce_partials(sum_partials, kPrepBlocks, 1, h->red_out, s));
 
@@ -789,6 +834,18 @@ pmace_status pmace_create(const pmace_dims* dims, const float* probe, const int3
             PM_CREATE(cudaMemcpy(h->err, &bit, sizeof(int), cudaMemcpyHostToDevice));
         }
     }
+#ifdef PMACE_DEBUG
+    // Bounds-checking build only: PMACE_INJECT_BAD_OFFSET=1 overwrites the
+    // last window's corner on the device with one past the image, after the
+    // stacks were initialised, for the tests of the device-side checks (a
+    // release build has no checks and must never see it).
+    if (const char* env = std::getenv("PMACE_INJECT_BAD_OFFSET")) {
+        if (std::atoi(env) != 0) {
+            const int2 bad = make_int2(D.n1, D.n2);
+            PM_CREATE(cudaMemcpy(h->offs + (J - 1), &bad, sizeof(int2), cudaMemcpyHostToDevice));
+        }
+    }
+#endif
 #undef PM_CREATE
     cudaFree(perm_d);
     h->iterations = 0;
@@ -948,7 +1005,39 @@ pmace_status pmace_get_image(pmace_handle h, float* out, int out_on_device, void
         PM_CUDA(h, cudaStreamSynchronize(s));
         if (errflag & 2)
             return fail(h, PMACE_ERR_TIMEOUT, "a bounded wait of the agent sweep's exchange gave up: the image may be wrong");
+        if (errflag & kErrBoundsBit)
+            return fail(h, PMACE_ERR_STATE, "a device-side bounds check failed (bounds-checking build): the image may be wrong");
     }
+    return PMACE_OK;
+}
+
+pmace_status pmace_debug_spectra(pmace_handle h, const pmace_step* step, float* out, void* stream) {
+    if (!h) return fail(nullptr, PMACE_ERR_INVALID_ARG, "NULL handle");
+    if (!out || !step) return fail(h, PMACE_ERR_INVALID_ARG, "out and step are required");
+    if (!(step->alpha >= 0.f) || !std::isfinite(step->alpha) || !(step->rho > 0.f && step->rho < 1.f))
+        return fail(h, PMACE_ERR_INVALID_ARG, "invalid step");
+    const int np = h->dims.np, J = h->dims.J;
+    if (!agent_variant_of(np, h->variant).exchange)
+        return fail(h, PMACE_ERR_UNSUPPORTED_SIZE, "the spectrum check needs an exchange plan (variant %d is not)",
+                    h->variant);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float2* dst = reinterpret_cast<float2*>(out);
+    pmace_status st = launch_iteration(h, step->alpha, step->rho, s, false, true, dst);
+    if (st != PMACE_OK) return st;
+    // kernel order (row g, column c hold frequencies rows[g], cols[c]) to natural order, through u (dead now)
+    const size_t P = (size_t)np * np;
+    std::vector<int> rows = amp_row_order(np, h->variant), cols, map(P);
+    dif_order(radices_of(np), 0, np, cols);
+    for (int g = 0; g < np; ++g)
+        for (int c = 0; c < np; ++c) map[(size_t)rows[g] * np + cols[c]] = g * np + c;
+    int* map_d = nullptr;
+    PM_CUDA(h, cudaMalloc(&map_d, P * sizeof(int)));
+    cudaError_t e = cudaMemcpyAsync(map_d, map.data(), P * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->u, dst, (size_t)J * P * sizeof(float2), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = launch_relayout_window(dst, h->u, map_d, J, np, (int)sizeof(float2), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(map_d);
+    if (e != cudaSuccess) return cuda_fail(h, e, "spectrum reordering");
     return PMACE_OK;
 }
 
@@ -959,8 +1048,8 @@ pmace_status pmace_get_patches(pmace_handle h, float* out, int out_on_device, vo
     const size_t JP = (size_t)h->dims.J * h->dims.np * h->dims.np;
     // u is dead between iterations (G consumed it), so it serves as staging
     float2* dst = out_on_device ? reinterpret_cast<float2*>(out) : h->u;
-    PM_CUDA(h, launch_patches_from_state(h->q, h->xbar, h->offs, dst, h->dims.J, h->dims.np,
-                                         h->dims.n2, 2.0f * h->rho_pending, s));
+    PM_CUDA(h, launch_patches_from_state(h->q, h->xbar, h->offs, dst, h->dims.J, h->dims.np, h->dims.n1,
+                                         h->dims.n2, 2.0f * h->rho_pending, h->err, s));
     if (!out_on_device) {
         PM_CUDA(h, cudaMemcpyAsync(out, dst, JP * sizeof(float2), cudaMemcpyDeviceToHost, s));
         PM_CUDA(h, cudaStreamSynchronize(s));
@@ -980,6 +1069,8 @@ pmace_status pmace_residual(pmace_handle h, double out[2], void* stream) {
     PM_CUDA(h, cudaMemcpyAsync(&errflag, h->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     PM_CUDA(h, cudaStreamSynchronize(s));
     if (errflag & 2) return fail(h, PMACE_ERR_TIMEOUT, "a bounded wait of the agent sweep's exchange gave up");
+    if (errflag & kErrBoundsBit)
+        return fail(h, PMACE_ERR_STATE, "a device-side bounds check failed (bounds-checking build)");
     out[0] = r[1] > 0 ? std::sqrt(r[0] / r[1]) : 0.0;
     out[1] = r[3] > 0 ? r[2] / r[3] : 0.0;
     return PMACE_OK;

@@ -22,6 +22,13 @@ __host__ __device__ constexpr RadixPlan radix_plan(int L) {
                     : RadixPlan{0, 0};
 }
 
+// Bit of the job's error word that the bounds checks of the PMACE_DEBUG
+// build set (a window offset outside the image, a window index outside
+// [0, J), a gather unit outside its tables); the checked access is then
+// clamped or skipped, so the build never reads or writes outside a job's
+// arrays, and the host reports PMACE_ERR_STATE.
+constexpr int kErrBoundsBit = 8;
+
 // Arguments of one agent sweep (steps S0-S5 of one iteration, all patches).
 struct AgentArgs {
     float2* q;              // [J][Np][Np] pending stack q = v - 2 rho w (read, then overwritten; the
@@ -36,13 +43,17 @@ struct AgentArgs {
     const int2* offs;       // [J] (row, col) window corners
     double* partials;       // [J * cluster][4] residual partial sums
     int n2;                 // image row stride (columns)
+    int n1;                 // image rows (bounds checks of the PMACE_DEBUG build)
     int J;
     float alpha, rho_prev, rho_cur;
     int first;              // 1 on the first iteration of the job
     int residual;           // 1: write the residual partial sums (else they are left untouched)
     int keep_u;             // 1: store u with the L2 evict-last hint (u fits about twice the L2)
     int wpc;                // windows per cluster (transposing-exchange variant)
-    int* err;               // bit 2 set when a bounded device-side wait gives up
+    int* err;               // bit 2: a bounded device-side wait gave up; bit 3: a bounds check of the
+                            // PMACE_DEBUG build failed
+    float2* spectrum;       // when set (exchange variants): the unnormalised forward 2-D DFT of d v of every
+                            // window, [J][Np][Np] in kernel order, written as the column step computes it
 };
 
 // Arguments of the pixel-owner gathers (weight image, consensus, readout).
@@ -61,6 +72,9 @@ struct GatherArgs {
     float* lam_out;         // weight-image mode: Lambda^-1 written here
     int n1, n2, np, tiles_x;
     float two_rho;          // readout: 2 rho
+    // bounds of the tables, checked by the PMACE_DEBUG build (bit 3 of *err)
+    int J, list_len, ntiles, nslots;
+    int* err;
 };
 
 // Gather tiles are kGatherTileW = 32 pixels wide (one warp per tile row
@@ -86,22 +100,25 @@ __host__ __device__ constexpr int gather_threads(int tile_h) {
 // windows per cluster, and how the 2-D DFT is split over the cluster
 // (exchange 0: an in-place cross-CTA butterfly stage through distributed
 // shared memory, agent.cuh; 1: a transposing exchange of 16 x 16 blocks by
-// bulk copies, Np / 16 CTAs, a run of windows per cluster, agent_xpose.cuh).
+// bulk copies, Np / 16 CTAs, a run of windows per cluster, agent_xpose.cuh;
+// 2: the same exchange with two windows at a time in packed FP32 lanes,
+// agent_pair.cuh, compiled for 128 x 128 probes only).
 // default_agent_variant is where a job starts; pmace_autotune and
-// PMACE_AGENT_PLAN pick others.
+// PMACE_AGENT_PLAN pick others.  A variant a probe size does not compile
+// reports cudaErrorInvalidValue from its agent entry and is never chosen.
 struct AgentVariant {
     int cluster, cols_per_thread, stage_y, windows, exchange;
 };
-constexpr int kAgentVariants = 5;
+constexpr int kAgentVariants = 6;
 __host__ __device__ constexpr AgentVariant agent_variant_of(int np, int v) {
     constexpr AgentVariant t32[kAgentVariants] = {
-        {2, 1, 1, 1, 0}, {1, 1, 1, 1, 0}, {2, 1, 0, 2, 0}, {1, 1, 0, 1, 0}, {2, 1, 0, 1, 1}};
+        {2, 1, 1, 1, 0}, {1, 1, 1, 1, 0}, {2, 1, 0, 2, 0}, {1, 1, 0, 1, 0}, {2, 1, 0, 1, 1}, {2, 1, 0, 2, 2}};
     constexpr AgentVariant t64[kAgentVariants] = {
-        {4, 1, 1, 1, 0}, {4, 2, 0, 1, 0}, {2, 1, 1, 1, 0}, {4, 1, 0, 2, 0}, {4, 1, 0, 1, 1}};
+        {4, 1, 1, 1, 0}, {4, 2, 0, 1, 0}, {2, 1, 1, 1, 0}, {4, 1, 0, 2, 0}, {4, 1, 0, 1, 1}, {4, 1, 0, 2, 2}};
     constexpr AgentVariant t128[kAgentVariants] = {
-        {8, 2, 0, 1, 0}, {8, 1, 1, 1, 0}, {4, 1, 1, 1, 0}, {8, 2, 0, 2, 0}, {8, 1, 0, 1, 1}};
+        {8, 2, 0, 1, 0}, {8, 1, 1, 1, 0}, {4, 1, 1, 1, 0}, {8, 2, 0, 2, 0}, {8, 1, 0, 1, 1}, {8, 1, 0, 2, 2}};
     constexpr AgentVariant t256[kAgentVariants] = {
-        {16, 2, 0, 1, 0}, {16, 2, 0, 2, 0}, {8, 1, 1, 1, 0}, {8, 2, 0, 1, 0}, {16, 1, 0, 1, 1}};
+        {16, 2, 0, 1, 0}, {16, 2, 0, 2, 0}, {8, 1, 1, 1, 0}, {8, 2, 0, 1, 0}, {16, 1, 0, 1, 1}, {16, 1, 0, 2, 2}};
     return np == 32 ? t32[v] : np == 64 ? t64[v] : np == 128 ? t128[v] : t256[v];
 }
 // The fastest variant measured on GB300 for each probe size: the in-place
@@ -145,18 +162,20 @@ cudaError_t launch_gather_readout(const GatherArgs& g, int nunits, int tile_h, c
 cudaError_t launch_gather_consensus_batched(const GatherArgs* descs, const int2* work, int nunits, int tile_h,
                                             cudaStream_t s);
 cudaError_t launch_prep_amps(const void* amps_in, int amp_f16, const float* scales, void* y_out,
-                             const int* rowperm, const int* colperm, int J, int np,
-                             double* sumsq_partials, int* err_flag, int nblocks, cudaStream_t s);
+                             const int* layout, int J, int np, double* sumsq_partials, int* err_flag,
+                             int nblocks, cudaStream_t s);
 cudaError_t launch_reduce_partials(const double* partials, int nrows, int ncols, double* out,
                                    cudaStream_t s);
 cudaError_t launch_init_stack(float2* q, const float2* init, float2 cval, const int2* offs,
                               int J, int np, int n2, cudaStream_t s);
 cudaError_t launch_patches_from_state(const float2* q, const float2* xbar, const int2* offs,
-                                      float2* v, int J, int np, int n2, float two_rho,
-                                      cudaStream_t s);
+                                      float2* v, int J, int np, int n1, int n2, float two_rho,
+                                      int* err, cudaStream_t s);
 cudaError_t launch_check_finite(const float* data, int64_t n, int* err_flag, cudaStream_t s);
-cudaError_t launch_relayout_rows(void* dst, const void* src, const int* rowmap, int J, int np, int elem,
-                                 cudaStream_t s);
+// dst[j][e] = src[j][map[e]] for every window j and stored position e
+// (elem bytes per value: 2, 4 or 8).
+cudaError_t launch_relayout_window(void* dst, const void* src, const int* map, int J, int np, int elem,
+                                   cudaStream_t s);
 
 // Message returned by pmace_last_error(NULL) (pmace_api.cu).
 void set_unbound_error(const char* msg);

@@ -37,6 +37,14 @@ __device__ __forceinline__ void gather_body(const GatherArgs& g, const int unit)
     __shared__ int s_last;
 
     const int4 un = __ldg(g.units + unit);          // (tile, lb, le, slot)
+#ifdef PMACE_DEBUG
+    // the unit must lie inside the tables (else the CTA flags it and stops)
+    if (un.x < 0 || un.x >= g.ntiles || un.y < 0 || un.y > un.z || un.z > g.list_len || un.w < -1 ||
+        un.w >= g.nslots) {
+        if (threadIdx.x == 0) atomicOr(g.err, kErrBoundsBit);
+        return;
+    }
+#endif
     const int tile = un.x;
     const int ty0 = (tile / g.tiles_x) * TH, tx0 = (tile % g.tiles_x) * TW;
     const int lane = threadIdx.x % TW, grp = threadIdx.x / TW;
@@ -56,9 +64,23 @@ __device__ __forceinline__ void gather_body(const GatherArgs& g, const int unit)
         const int n = min(kGatherStage, un.z - cb);
         if (cb != un.y) __syncthreads();            // the previous chunk is consumed
         if (threadIdx.x < n) {
-            const int i = __ldg(g.tile_list + cb + threadIdx.x);
+            int i = __ldg(g.tile_list + cb + threadIdx.x);
+#ifdef PMACE_DEBUG
+            // a window index outside [0, J) or a corner outside the image is
+            // flagged and the window left out (a corner far outside every tile)
+            const bool bad_i = i < 0 || i >= g.J;
+            if (bad_i) i = 0;
+            int2 o = __ldg(g.offs + i);
+            if (bad_i || o.x < 0 || o.x > g.n1 - np || o.y < 0 || o.y > g.n2 - np) {
+                atomicOr(g.err, kErrBoundsBit);
+                o = make_int2(-(1 << 29), -(1 << 29));
+            }
+            s_i[threadIdx.x] = i;
+            s_o[threadIdx.x] = o;
+#else
             s_i[threadIdx.x] = i;
             s_o[threadIdx.x] = __ldg(g.offs + i);
+#endif
         }
         __syncthreads();
         // Windows are taken U at a time so that U * RPT loads are in flight
@@ -197,17 +219,19 @@ cudaError_t launch_gather_consensus_batched(const GatherArgs* descs, const int2*
 }
 
 // ---------------------------------------------------------------------------
-// Amplitudes to kernel order: y_k[j][r][c] = y[j][colperm[r]][rowperm[c]]
-// (the digit-reversed order the in-place DIF stages leave the spectrum in),
-// validating finiteness and sign, and FP64 partial sums of y^2 per block.
+// Amplitudes to the agent kernel's layout: y_k[j][e] = y[j][layout[e]], where
+// layout[e] is the natural index (frequency row * np + frequency column) of
+// stored position e (the digit-reversed order the in-place DIF stages leave
+// the spectrum in, in the agent variant's thread order), validating
+// finiteness and sign, and FP64 partial sums of y^2 per block.
 // ---------------------------------------------------------------------------
 constexpr int kPrepThreads = 256;
 
 template <int F16>
 __global__ void __launch_bounds__(kPrepThreads)
 prep_amps_kernel(const void* __restrict__ in, const float* __restrict__ scales, void* __restrict__ out,
-                 const int* __restrict__ rowperm, const int* __restrict__ colperm, int J, int np,
-                 double* __restrict__ partials, int* __restrict__ err) {
+                 const int* __restrict__ layout, int J, int np, double* __restrict__ partials,
+                 int* __restrict__ err) {
     const size_t P = (size_t)np * np;
     const size_t total = (size_t)J * P;
     double s = 0.0;
@@ -216,8 +240,7 @@ prep_amps_kernel(const void* __restrict__ in, const float* __restrict__ scales, 
          idx += (size_t)gridDim.x * kPrepThreads) {
         const size_t j = idx / P;
         const int e = (int)(idx % P);
-        const int r = e / np, c = e % np;
-        const size_t src = j * P + (size_t)colperm[r] * np + rowperm[c];
+        const size_t src = j * P + (size_t)layout[e];
         float v;
         if constexpr (F16) {
             const __half h = static_cast<const __half*>(in)[src];
@@ -245,14 +268,12 @@ prep_amps_kernel(const void* __restrict__ in, const float* __restrict__ scales, 
 }
 
 cudaError_t launch_prep_amps(const void* amps_in, int amp_f16, const float* scales, void* y_out,
-                             const int* rowperm, const int* colperm, int J, int np,
-                             double* partials, int* err, int nblocks, cudaStream_t s) {
+                             const int* layout, int J, int np, double* partials, int* err, int nblocks,
+                             cudaStream_t s) {
     if (amp_f16)
-        prep_amps_kernel<1><<<nblocks, kPrepThreads, 0, s>>>(amps_in, scales, y_out, rowperm, colperm,
-                                                            J, np, partials, err);
+        prep_amps_kernel<1><<<nblocks, kPrepThreads, 0, s>>>(amps_in, scales, y_out, layout, J, np, partials, err);
     else
-        prep_amps_kernel<0><<<nblocks, kPrepThreads, 0, s>>>(amps_in, scales, y_out, rowperm, colperm,
-                                                            J, np, partials, err);
+        prep_amps_kernel<0><<<nblocks, kPrepThreads, 0, s>>>(amps_in, scales, y_out, layout, J, np, partials, err);
     return cudaGetLastError();
 }
 
@@ -316,14 +337,20 @@ cudaError_t launch_init_stack(float2* q, const float2* init, float2 cval, const 
 // v = q + 2 rho P_j xbar, the current Algorithm 1 stack.
 __global__ void patches_kernel(const float2* __restrict__ q, const float2* __restrict__ xbar,
                                const int2* __restrict__ offs, float2* __restrict__ v, int J, int np,
-                               int n2, float two_rho) {
+                               int n1, int n2, float two_rho, int* __restrict__ err) {
     const size_t P = (size_t)np * np;
     const size_t total = (size_t)J * P;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const size_t j = idx / P;
         const int e = (int)(idx % P);
-        const int2 o = offs[j];
+        int2 o = offs[j];
+#ifdef PMACE_DEBUG
+        if (o.x < 0 || o.x > n1 - np || o.y < 0 || o.y > n2 - np) {
+            atomicOr(err, kErrBoundsBit);
+            o = make_int2(min(max(o.x, 0), n1 - np), min(max(o.y, 0), n2 - np));
+        }
+#endif
         const float2 xb = xbar[(size_t)(o.x + e / np) * n2 + (o.y + e % np)];
         const float2 qv = q[idx];
         v[idx] = make_float2(fmaf(two_rho, xb.x, qv.x), fmaf(two_rho, xb.y, qv.y));
@@ -331,30 +358,37 @@ __global__ void patches_kernel(const float2* __restrict__ q, const float2* __res
 }
 
 cudaError_t launch_patches_from_state(const float2* q, const float2* xbar, const int2* offs,
-                                      float2* v, int J, int np, int n2, float two_rho,
-                                      cudaStream_t s) {
-    patches_kernel<<<1216, 256, 0, s>>>(q, xbar, offs, v, J, np, n2, two_rho);
+                                      float2* v, int J, int np, int n1, int n2, float two_rho,
+                                      int* err, cudaStream_t s) {
+    patches_kernel<<<1216, 256, 0, s>>>(q, xbar, offs, v, J, np, n1, n2, two_rho, err);
     return cudaGetLastError();
 }
 
-// Row permutation of a [J][np][np] stack of elem-byte values:
-// dst[j][g][c] = src[j][rowmap[g]][c].
-__global__ void relayout_rows_kernel(char* __restrict__ dst, const char* __restrict__ src,
-                                     const int* __restrict__ rowmap, int J, int np, int elem) {
-    const size_t row_bytes = (size_t)np * elem;
-    const size_t total = (size_t)J * np * row_bytes;
+// Per-window permutation of a [J][np * np] stack of elem-byte values:
+// dst[j][e] = src[j][map[e]] (elem 2, 4 or 8).
+template <typename E>
+__global__ void relayout_window_kernel(E* __restrict__ dst, const E* __restrict__ src, const int* __restrict__ map,
+                                       int J, int np) {
+    const size_t P = (size_t)np * np, total = (size_t)J * P;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t rowi = i / row_bytes, b = i % row_bytes;
-        const size_t j = rowi / np;
-        const int g = (int)(rowi % np);
-        dst[i] = src[(j * np + rowmap[g]) * row_bytes + b];
+        const size_t j = i / P;
+        dst[i] = src[j * P + map[i % P]];
     }
 }
 
-cudaError_t launch_relayout_rows(void* dst, const void* src, const int* rowmap, int J, int np, int elem,
-                                 cudaStream_t s) {
-    relayout_rows_kernel<<<1216, 256, 0, s>>>(static_cast<char*>(dst), static_cast<const char*>(src), rowmap,
-                                              J, np, elem);
+cudaError_t launch_relayout_window(void* dst, const void* src, const int* map, int J, int np, int elem,
+                                   cudaStream_t s) {
+    if (elem == 2)
+        relayout_window_kernel<unsigned short><<<1216, 256, 0, s>>>(static_cast<unsigned short*>(dst),
+                                                                    static_cast<const unsigned short*>(src), map, J, np);
+    else if (elem == 4)
+        relayout_window_kernel<float><<<1216, 256, 0, s>>>(static_cast<float*>(dst), static_cast<const float*>(src),
+                                                           map, J, np);
+    else if (elem == 8)
+        relayout_window_kernel<float2><<<1216, 256, 0, s>>>(static_cast<float2*>(dst), static_cast<const float2*>(src),
+                                                            map, J, np);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

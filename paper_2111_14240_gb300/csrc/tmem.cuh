@@ -12,8 +12,18 @@
 
 namespace pmace {
 
+// One allocation, after which the CTA gives up its right to allocate.
 __device__ __forceinline__ void tmem_alloc(uint32_t smem_dst, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_dst), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+// Two allocations (ncols0 and ncols1 columns, each a power of 2 >= 32),
+// then the CTA gives up its right to allocate.
+__device__ __forceinline__ void tmem_alloc2(uint32_t smem_dst0, uint32_t ncols0, uint32_t smem_dst1, uint32_t ncols1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_dst0), "r"(ncols0)
+                 : "memory");
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_dst1), "r"(ncols1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }

@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_PKG, "libpmace.so")
+# PMACE_LIBRARY selects another build of the library (for example the
+# bounds-checking libpmace_debug.so); default: the in-tree libpmace.so
+_LIB_PATH = os.environ.get("PMACE_LIBRARY") or os.path.join(_PKG, "libpmace.so")
 
 PMACE_OK = 0
 PMACE_ERR_INVALID_ARG = 1
@@ -79,7 +81,7 @@ EXPORTS = ["pmace_create", "pmace_iterate", "pmace_get_image", "pmace_get_patche
            "pmace_amplitude_energy_noalloc", "pmace_set_plan", "pmace_autotune",
            "pmace_server_create", "pmace_server_submit", "pmace_server_poll", "pmace_server_wait",
            "pmace_server_release", "pmace_server_stats", "pmace_server_destroy",
-           "pmace_simulate", "pmace_photon_noise", "pmace_selftest_bounded_wait"]
+           "pmace_simulate", "pmace_photon_noise", "pmace_selftest_bounded_wait", "pmace_debug_spectra"]
 
 
 # ABI version of include/pmace.h that the structures below mirror
@@ -125,6 +127,7 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
                                  ctypes.c_int, vp]),
         "pmace_photon_noise": (i32, [vp, i32, i32, ctypes.c_double, ctypes.c_uint64, vp, ctypes.c_int, vp]),
         "pmace_selftest_bounded_wait": (i32, [vp]),
+        "pmace_debug_spectra": (i32, [vp, P(pmace_step), vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -291,6 +294,14 @@ def photon_noise(intensity, peak, seed=0, stream=None):
     _check(_lib.pmace_photon_noise(_ptr(inten), int(J), int(n1), float(peak), int(seed) & (2**64 - 1),
                                    _ptr(out), 0, _stream(stream)), None)
     return out
+
+
+def pmace_debug_spectra(h, alpha, rho, out, stream=None):
+    """One iteration that also writes every window's forward 2-D DFT
+    F (d v_j), unnormalised, natural order, into the device tensor `out`
+    (J, np, np, 2) float32 (include/pmace.h)."""
+    step = pmace_step(float(alpha), float(rho))
+    _check(_lib.pmace_debug_spectra(h, ctypes.byref(step), _ptr(out), _stream(stream)), h)
 
 
 def pmace_set_plan(h, variant, tile_h, stream=None):

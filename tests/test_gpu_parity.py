@@ -78,7 +78,7 @@ def test_one_iteration_np64(variant):
     assert g["plan"]["variant"] == variant
 
 
-@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("variant", VARIANTS + [5])
 def test_one_iteration_np128(variant):
     w = datagen.make_workload(dict(MID128, name="mid128"), seed=4)
     g, _ = _check_iteration(w, 1, variant=variant)
@@ -93,17 +93,19 @@ def test_one_iteration_np256_full_config(variant):
     assert g["plan"]["variant"] == variant
 
 
-@pytest.mark.parametrize("cfg,wpc", [("small", 4), ("mid64", 5), ("mid128", 7)])
-def test_exchange_variant_runs_of_windows(cfg, wpc, monkeypatch):
-    """The transposing-exchange variant with a fixed run of windows per
-    cluster (the last run shorter), three iterations: the per-slab barriers
-    are re-armed window after window and iteration after iteration."""
+@pytest.mark.parametrize("cfg,wpc,variant", [("small", 4, 4), ("mid64", 5, 4), ("mid128", 7, 4), ("mid128", 6, 5),
+                                              ("mid128", 2, 5)])
+def test_exchange_variant_runs_of_windows(cfg, wpc, variant, monkeypatch):
+    """The transposing-exchange variants with a fixed run of windows per
+    cluster (the last run shorter; for the two-window variant the last run
+    ends in a single window), three iterations: the per-slab barriers are
+    re-armed window after window and iteration after iteration."""
     spec = {"small": "small", "mid64": dict(MID64, name="mid64"), "mid128": dict(MID128, name="mid128")}[cfg]
     w = datagen.make_workload(spec, seed=31)
     assert w.J % wpc != 0
     monkeypatch.setenv("PMACE_AGENT_WPC", str(wpc))
-    g, _ = _check_iteration(w, 3, variant=4)
-    assert g["plan"]["exchange"] == 1 and g["plan"]["windows_per_cluster"] == wpc
+    g, _ = _check_iteration(w, 3, variant=variant)
+    assert g["plan"]["exchange"] == (1 if variant == 4 else 2) and g["plan"]["windows_per_cluster"] == wpc
 
 
 def _midrun_step(w, k, alpha=0.5, rho=0.5, variant=None):
@@ -282,3 +284,35 @@ def test_rejects_negative_amplitudes_on_device():
     with pytest.raises(pm.PmaceError) as e:
         pm.Reconstruction(w.probe, w.offsets, torch.from_numpy(y).cuda(), w.x.shape)
     assert e.value.status == pm.PMACE_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("cfg,variant", [("small", 4), ("mid64", 4), ("mid128", 4), ("mid128", 5), ("p256", 4)])
+def test_forward_transform_stage_matches_fft(cfg, variant):
+    """The agent sweep's forward 2-D DFT on its own (the exchange plans' row
+    and column stages, before the magnitude replacement, Section III-A)
+    against numpy's orthonormal FFT of d v_j for every window, the
+    digit-reversed order undone: from a start image the first iteration's
+    agent input is v_j = P_j x0."""
+    import torch
+
+    from paper_2111_14240_gb300 import pmace as pm
+    from tests.gpu_helpers import plan_env
+    spec = {"small": "small", "mid64": dict(MID64, name="mid64"), "mid128": dict(MID128, name="mid128"),
+            "p256": "p256"}[cfg]
+    w = datagen.make_workload(spec, seed=41)
+    _, _, probe32, y32 = rounded_inputs(w)
+    x0 = random_start(w)
+    with plan_env(variant):
+        rec = pm.Reconstruction(probe32, w.offsets, y32, w.x.shape, init=x0)
+    try:
+        assert rec.plan()["variant"] == variant
+        out = torch.empty((w.J, w.np_, w.np_, 2), dtype=torch.float32, device="cuda")
+        pm.pmace_debug_spectra(rec.h, 0.5, 0.5, out)
+        got = torch.view_as_complex(out).cpu().numpy().astype(np.complex128) / w.np_
+    finally:
+        rec.close()
+    v = np.stack([x0[r:r + w.np_, c:c + w.np_] for r, c in w.offsets]).astype(np.complex128)
+    ref = np.fft.fft2(probe32.astype(np.complex128)[None] * v, norm="ortho")
+    e = rel_l2(got, ref)
+    print(f"{cfg} variant {variant}: forward transform rel-L2 {e:.2e}")
+    assert e < 2e-6
