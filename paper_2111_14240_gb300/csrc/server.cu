@@ -5,16 +5,18 @@
 // admitter thread creates queued jobs in arrival order while the device
 // bytes of the admitted jobs stay within the budget, a slot is free and the
 // admitted jobs do not already fill a tick; a worker thread runs the ticks.
-// Every job
-// keeps its whole state resident (stacks, consensus image, amplitudes).  One
-// tick runs one iteration of Algorithm 1 for every admitted job: one agent
-// launch per (probe size, amplitude format, plan) group, whose clusters
-// cover the windows of all the jobs in the group, and one consensus launch
-// whose CTAs cover the image tiles of all the jobs.  A job that reaches its
-// iteration count is read out and retired at the end of the tick, which
-// frees its memory and slot for the next queued job.  Each window and each
-// pixel is computed by the same code as in a job run alone, so a job's
-// result does not depend on what it was batched with.
+// Every job keeps its whole state resident (stacks, consensus image,
+// amplitudes).  One tick runs one iteration of Algorithm 1 for the admitted
+// jobs it steps: one agent launch per (probe size, amplitude format, plan)
+// group, whose clusters cover the windows of all the stepped jobs in the
+// group, and one consensus launch whose CTAs cover their image tiles.  A
+// tick steps every admitted job while they fit the device; when they hold
+// more work than that, it steps the jobs with the least remaining work
+// first (see tick()).  A job that reaches its iteration count is read out
+// and retired at the end of the tick, which frees its memory and slot for
+// the next queued job.  Each window and each pixel is computed by the same
+// code as in a job run alone, so a job's result does not depend on what it
+// was batched with or on which ticks stepped it.
 #include "job.h"
 #include "pmace.h"
 #include "pmace_internal.h"
@@ -24,6 +26,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -61,7 +64,12 @@ struct Active {
     pmace_job* job = nullptr;
     double start_ms = 0.0;
     int64_t bytes = 0;
+    int32_t skipped = 0;   // consecutive ticks this job waited for shorter ones
 };
+
+// A job is stepped at the latest after this many consecutive ticks in
+// which shorter jobs filled the device.
+constexpr int32_t kMaxSkippedTicks = 64;
 
 struct Result {
     pmace_status status = PMACE_OK;
@@ -111,6 +119,7 @@ struct pmace_server {
     int32_t max_active = 0;
     int32_t tile_h = 16;
     int64_t fill_pixels = 0;           // admit while the active jobs' window pixels per tick stay below this
+    int64_t tick_pixels = 0;           // window pixels per tick that fill the device
     cudaStream_t stream = nullptr;     // ticks and readouts
     cudaStream_t admit_stream = nullptr;  // job creation, so admission does not wait for queued ticks
 
@@ -261,14 +270,38 @@ void pmace_server::admit_loop() {
     }
 }
 
-// One iteration for every admitted job that still has iterations to run.
+// One iteration for admitted jobs that still have iterations to run: the
+// jobs with the least remaining work first (window pixels times remaining
+// iterations, then arrival order), as many as fill the device
+// (tick_pixels window pixels); a job that has waited kMaxSkippedTicks ticks
+// is stepped regardless.  Short jobs then finish without waiting behind
+// long ones, while the device stays full.  Which ticks step a job does not
+// change its arithmetic.
 pmace_status pmace_server::tick() {
+    std::vector<int> cand;
+    for (int i = 0; i < (int)active.size(); ++i)
+        if (active[i].job->iterations < active[i].req.iterations) cand.push_back(i);
+    auto remaining = [&](int i) {
+        const pmace_job* h = active[i].job;
+        return (int64_t)h->dims.J * h->dims.np * h->dims.np * (active[i].req.iterations - h->iterations);
+    };
+    std::stable_sort(cand.begin(), cand.end(), [&](int x, int y) {
+        const int64_t rx = remaining(x), ry = remaining(y);
+        return rx != ry ? rx < ry : active[x].req.id < active[y].req.id;
+    });
     // agent launches, one per (probe size, amplitude format, variant) group
     std::map<std::tuple<int, int, int>, std::vector<int>> groups;
-    for (int i = 0; i < (int)active.size(); ++i) {
-        const pmace_job* h = active[i].job;
-        if (h->iterations < active[i].req.iterations)
+    int64_t px = 0;
+    for (int i : cand) {
+        Active& a = active[i];
+        const pmace_job* h = a.job;
+        if (px < tick_pixels || a.skipped >= kMaxSkippedTicks) {
             groups[std::make_tuple(h->dims.np, h->amp_f16, h->variant)].push_back(i);
+            px += (int64_t)h->dims.J * h->dims.np * h->dims.np;
+            a.skipped = 0;
+        } else {
+            a.skipped++;
+        }
     }
     if (groups.empty()) return PMACE_OK;
     std::vector<AgentArgs> adesc;
@@ -424,6 +457,13 @@ pmace_status pmace_server_create(const pmace_server_config* cfg, pmace_server_ha
     const int th = cfg ? cfg->tile_h : 0;
     sv->tile_h = (th == 8 || th == 16 || th == 32) ? th : 16;
     sv->fill_pixels = (cfg && cfg->fill_pixels > 0) ? cfg->fill_pixels : ((int64_t)1 << 27);
+    // about a thousand 128 x 128 windows fill every SM with agent clusters
+    // more than once (PMACE_SERVER_TICK_PIXELS overrides)
+    sv->tick_pixels = (int64_t)1 << 24;
+    if (const char* env = std::getenv("PMACE_SERVER_TICK_PIXELS")) {
+        const long long v = std::atoll(env);
+        if (v > 0) sv->tick_pixels = v;
+    }
     e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->admit_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
