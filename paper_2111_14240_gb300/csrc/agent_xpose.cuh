@@ -92,6 +92,18 @@ struct XposeGeom {
     static_assert(S1 * r1 == N, "one twiddle table entry per (stage output, butterfly)");
 };
 
+// First-stage butterfly of a row stage handled by thread slot id (0 ..
+// 16 S1 - 1): slab row k, butterfly b (elements b + S1 t).  A half-warp
+// takes 16 / S1 rows S1 apart (k = id / 16 + S1 * row of the half-warp),
+// so that with rows padded to 17 elements its 16 eight-byte accesses fall
+// in 16 different bank pairs (rows k and k + 1 side by side would share
+// seven of them), while a warp still reads S1 consecutive elements of each
+// of its rows from global memory.
+__device__ __forceinline__ void row_butterfly(int id, int S1, int& k, int& b) {
+    k = id / 16 + S1 * ((id % 16) / S1);
+    b = id % S1;
+}
+
 // Slab index of element (k, c) of block blk (16 rows of 17 elements).
 __device__ __forceinline__ int xslab(int blk, int k, int c) { return blk * 272 + k * 17 + c; }
 // Row slab: window row k of the CTA, storage column s.
@@ -258,7 +270,8 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
         const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
         tm_addr = tm_sh + lanes + 64u * (uint32_t)(warp >> 2);
         if constexpr (kTmD) tm_d = tm_sh_d + lanes + 32u * (uint32_t)(warp >> 2);
-        const int k = threadIdx.x / S1, b = threadIdx.x % S1;
+        int k, b;
+        row_butterfly(threadIdx.x, S1, k, b);
         const float2* dr = a.dinv + (size_t)(row0 + k) * N;
         const float2* pr = a.probe + (size_t)(row0 + k) * N;
 #pragma unroll
@@ -303,7 +316,8 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
         // ---- S0 + S1 fused with the first DIF row stage (span N, radix r1)
 #pragma unroll 1
         for (int id = threadIdx.x; id < G::NB1; id += T) {
-            const int k = id / S1, b = id % S1;
+            int k, b;
+            row_butterfly(id, S1, k, b);
             const int row = row0 + k;
             const float2* qr = a.q + wbase + (size_t)row * N;
             const float2* __restrict__ dr = a.probe + (size_t)row * N;
@@ -486,7 +500,8 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
         float acc_z = 0.f, acc_w = 0.f;
 #pragma unroll 1
         for (int id = threadIdx.x; id < G::NB1; id += T) {
-            const int k = id / S1, b = id % S1;
+            int k, b;
+            row_butterfly(id, S1, k, b);
             const int row = row0 + k;
             float2 x[r1];
 #pragma unroll
