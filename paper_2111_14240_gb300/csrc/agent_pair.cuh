@@ -422,11 +422,18 @@ __device__ __forceinline__ void pair_body(const AgentArgs& a, const int j0, cons
         for (int h = 0; h < 4; ++h) load_quarter(ps, h);
     }
 
+    // window corners loaded a pair ahead, so the consensus loads of the
+    // copy-in do not wait for them
+    int2 off_next0 = window_corner<N>(a, j0), off_next1 = window_corner<N>(a, j0 + 1 < jn ? j0 + 1 : j0);
 #pragma unroll 1
     for (int j = j0; j < jn; j += 2) {
         const bool two = j + 1 < jn;
         const int jb = two ? j + 1 : j;   // lane 1 repeats lane 0 at an odd end
-        const int2 off0 = window_corner<N>(a, j), off1 = window_corner<N>(a, jb);
+        const int2 off0 = off_next0, off1 = off_next1;
+        if (j + 2 < jn) {   // the next pair's corners, a pair ahead
+            off_next0 = window_corner<N>(a, j + 2);
+            off_next1 = window_corner<N>(a, j + 3 < jn ? j + 3 : j + 2);
+        }
         const size_t wb0 = (size_t)j * N * N, wb1 = (size_t)jb * N * N;
         float2 ysc = make_float2(1.f, 1.f);
         if constexpr (AMP == 1) ysc = make_float2(__ldg(a.yscale + j), __ldg(a.yscale + jb));

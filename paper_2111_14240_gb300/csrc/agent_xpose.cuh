@@ -305,9 +305,13 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
     };
     prefetch_window(j0);
 
+    // the window corner is loaded a window ahead, so the consensus loads of
+    // the copy-in do not wait for it
+    int2 off_next = window_corner<N>(a, j0);
 #pragma unroll 1
     for (int j = j0; j < jn; ++j) {
-        const int2 off = window_corner<N>(a, j);
+        const int2 off = off_next;
+        if (j + 1 < jn) off_next = window_corner<N>(a, j + 1);
         const size_t wbase = (size_t)j * N * N;
         float yscale = 1.0f;
         if constexpr (AMP == 1) yscale = __ldg(a.yscale + j);
@@ -523,8 +527,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
                     // v and 1/d from TMEM; the consensus values only feed the residual
                     static_assert(H == 4, "one 8-column TMEM load per quarter and table");
                     uint32_t rv[8], rd[8];
-                    tmem_ld8(tm_addr + 32u + 2u * (uint32_t)h0, rv);
-                    tmem_ld8(tm_addr + 2u * (uint32_t)h0, rd);
+                    tmem_ld8x2(tm_addr + 32u + 2u * (uint32_t)h0, rv, tm_addr + 2u * (uint32_t)h0, rd);
 #pragma unroll
                     for (int t = 0; t < H; ++t) {
                         qv[t] = make_float2(__uint_as_float(rv[2 * t]), __uint_as_float(rv[2 * t + 1]));
