@@ -287,6 +287,11 @@ def host_info():
 
 
 # ------------------------------------------------------------------ inputs
+# --scan n: an n x n sub-raster of the headline workload's scan (the same
+# object, probe and step), for profiling captures of a few GB
+SCAN_OVERRIDE = {}
+
+
 @functools.lru_cache(maxsize=2)
 def scan_geometry(name: str, seed: int = 1):
     """Object, probe and scan offsets of a workload, drawn in the generator's
@@ -296,7 +301,8 @@ def scan_geometry(name: str, seed: int = 1):
     rng = np.random.Generator(np.random.PCG64(seed))
     x = datagen.make_object(rng, c["n_obj"], c["n_obj"])
     probe = datagen.make_probe(rng, c["n_p"], c["probe_sigma"])
-    offs = datagen.make_offsets(rng, c["n_obj"], c["n_p"], c["n_scan"], c["step"], c["jitter"])
+    offs = datagen.make_offsets(rng, c["n_obj"], c["n_p"], SCAN_OVERRIDE.get(name, c["n_scan"]), c["step"],
+                                c["jitter"])
     return x, probe, offs
 
 
@@ -578,7 +584,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP16 amplitudes)" if f16 else "f32",
         "data": "synthetic (seeded generator; amplitudes by the GPU simulator)",
-        "config": {"workload": desc, "windows": J, "probe": np_, "image": [n1, n2],
+        "config": {"workload": desc if not args.scan else f"{args.scan}x{args.scan} sub-raster of: {desc}",
+                   "windows": J, "probe": np_, "image": [n1, n2],
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "no flush: per-step working set (q, u, y) is "
                          f"{(J * np_ * np_ * (16 + amp_b)) / 1e9:.2f} GB > 129 MB L2",
@@ -900,6 +907,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS),
                     help="the headline workload (default: the 64009-window 8192^2 scan)")
+    ap.add_argument("--scan", type=int, default=0,
+                    help="n x n sub-raster of the workload's scan (profiling captures; 0: the full scan)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="seconds of oracle work per CPU-baseline variant")
     ap.add_argument("--cpu-max-windows", type=int, default=4096)
@@ -922,6 +931,8 @@ def main():
     ap.add_argument("--precision", action="store_true",
                     help="FP16 against FP32 amplitudes on the 14641-window workload")
     args = ap.parse_args()
+    if args.scan > 0:
+        SCAN_OVERRIDE[args.workload] = args.scan
     if args.serve:
         return run_serve(args)
     if args.convergence:
