@@ -104,6 +104,47 @@ __device__ __forceinline__ float2 replace_magnitude(float2 xa, float y, float in
     return o;
 }
 
+// 1/sqrt(m) by the hardware approximation, for a normal m: there it is the
+// value rsqrtf gives, without rsqrtf's handling of subnormal arguments.
+__device__ __forceinline__ float rsqrt_normal(float m) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(m));
+    return r;
+}
+
+// S3 for the R coefficients of one butterfly, with the arithmetic of
+// replace_magnitude.  When every |A|^2 is at least 2^-100 (a normal number,
+// so neither the rescaling nor the zero test applies) a coefficient costs
+// its squared magnitude, one reciprocal square root and three
+// multiplications; otherwise (rare: a coefficient that is tiny, zero or
+// not finite) all R take the general path.
+template <bool RES, int R>
+__device__ __forceinline__ void replace_magnitudes(float2 (&x)[R], const float (&y)[R], float inv_n, float& acc_d,
+                                                   float& acc_y) {
+    float m2[R];
+    bool general = false;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        m2[i] = fmaf(x[i].x, x[i].x, x[i].y * x[i].y);
+        general |= !(m2[i] >= 0x1p-100f);
+    }
+    if (general) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[i] = replace_magnitude<RES>(x[i], y[i], inv_n, acc_d, acc_y);
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const float rs = rsqrt_normal(m2[i]);
+        if constexpr (RES) {
+            const float e = y[i] - m2[i] * rs * inv_n;
+            acc_d = fmaf(e, e, acc_d);
+            acc_y = fmaf(y[i], y[i], acc_y);
+        }
+        x[i] = x[i] * (y[i] * rs);
+    }
+}
+
 // Window corner j of the job, checked against the image in the PMACE_DEBUG
 // build (a corner outside [0, n1 - N] x [0, n2 - N] sets the bounds bit of
 // the error word and is clamped into range).
@@ -139,6 +180,25 @@ __device__ __forceinline__ float2 agent_step(float2 g, float2 v, float2 dv, floa
     }
     u = make_float2(2.f * w.x - v.x, 2.f * w.y - v.y);
     qn = make_float2(fmaf(-two_rho, w.x, v.x), fmaf(-two_rho, w.y, v.y));
+    return w;
+}
+
+// mann_close and agent_step with packed FP32 instructions (each lane
+// rounded exactly as the scalar form); the constants come as lane pairs:
+// trp2 = (2 rho_prev, 2 rho_prev), scale2 = (1/Np, 1/Np), alpha2, inv1pa2
+// = (1/(1+alpha), 1/(1+alpha)), m2rho2 = (-2 rho, -2 rho).  CHECK: test
+// for a probe value treated as absent (dv = 0) at this pixel; without it
+// the caller knows there is none.
+__device__ __forceinline__ float2 mann_close2(float2 q, float2 xv, float2 trp2) { return __ffma2_rn(trp2, xv, q); }
+template <bool CHECK>
+__device__ __forceinline__ float2 agent_step2(float2 g, float2 v, float2 dv, float2 scale2, float2 alpha2,
+                                              float2 inv1pa2, float2 m2rho2, float2& u, float2& qn) {
+    float2 w = __fmul2_rn(__ffma2_rn(alpha2, v, cmul(dv, __fmul2_rn(g, scale2))), inv1pa2);
+    if constexpr (CHECK) {
+        if (dv.x == 0.f && dv.y == 0.f) w = v;
+    }
+    u = __ffma2_rn(make_float2(2.f, 2.f), w, make_float2(-v.x, -v.y));
+    qn = __ffma2_rn(m2rho2, w, v);
     return w;
 }
 

@@ -236,6 +236,9 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
     const float inv1pa = 1.0f / (1.0f + a.alpha);
     const float alpha = a.alpha;
     const float two_rho = 2.0f * a.rho_cur;
+    const float2 trp2 = make_float2(two_rho_prev, two_rho_prev), scale2 = make_float2(scale, scale);
+    const float2 alpha2 = make_float2(alpha, alpha), inv1pa2 = make_float2(inv1pa, inv1pa);
+    const float2 m2rho2 = make_float2(-two_rho, -two_rho);
     const bool first = a.first != 0;
     const bool res = a.residual != 0;
     const int row0 = rank * G::R;
@@ -258,6 +261,9 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
     static_assert(!kTm || kTmCols * G::kMinBlocks <= 512, "TMEM of the resident CTAs must fit an SM");
     __shared__ uint32_t tm_sh, tm_sh_d;
     uint32_t tm_addr = 0, tm_d = 0;
+    // whether one of the thread's pixels has its probe value treated as
+    // absent (1/d = 0): only then does the update test for it
+    bool absent = !kTm;
     if constexpr (kTm) {
         if (threadIdx.x < 32) {
             if constexpr (kTmD) tmem_alloc2(smem_addr(&tm_sh), kTmCols, smem_addr(&tm_sh_d), kTmDCols);
@@ -280,6 +286,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
                 const float2 di = __ldg(dr + b + S1 * (8 * h + t));
+                absent |= di.x == 0.f && di.y == 0.f;
                 r[2 * t] = __float_as_uint(di.x);
                 r[2 * t + 1] = __float_as_uint(di.y);
                 if constexpr (kTmD) {
@@ -319,7 +326,8 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
 
         // ---- S0 + S1 fused with the first DIF row stage (span N, radix r1)
 #pragma unroll 1
-        for (int id = threadIdx.x; id < G::NB1; id += T) {
+        for (int it = 0; it < G::NB1 / T; ++it) {
+            const int id = threadIdx.x + it * T;
             int k, b;
             row_butterfly(id, S1, k, b);
             const int row = row0 + k;
@@ -332,7 +340,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
 #pragma unroll
             for (int t = 0; t < r1; ++t) x[t] = qr[b + S1 * t];
 #pragma unroll
-            for (int t = 0; t < r1; ++t) x[t] = mann_close(x[t], __ldg(xr + b + S1 * t), two_rho_prev);
+            for (int t = 0; t < r1; ++t) x[t] = mann_close2(x[t], __ldg(xr + b + S1 * t), trp2);
             if constexpr (kTm) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {   // keep v for the copy-out
@@ -385,7 +393,8 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
         __syncthreads();
         // ---- second DIF row stage (span r2)
 #pragma unroll 1
-        for (int id = threadIdx.x; id < G::NB2; id += T) {
+        for (int it = 0; it < G::NB2 / T; ++it) {
+            const int id = threadIdx.x + it * T;
             const int k = id % 16, m = id / 16;
             float2 x[r2];
 #pragma unroll
@@ -423,7 +432,8 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
 
         // ---- first DIF column stage (span N, radix r1)
 #pragma unroll 1
-        for (int id = threadIdx.x; id < G::NB1; id += T) {
+        for (int it = 0; it < G::NB1 / T; ++it) {
+            const int id = threadIdx.x + it * T;
             const int c = id % 16, b = id / 16;
             float2 x[r1];
 #pragma unroll
@@ -453,8 +463,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
 #pragma unroll
                     for (int i = 0; i < r2; ++i) a.spectrum[wbase + (size_t)(m * r2 + i) * N + row0 + c] = x[i];
                 }
-#pragma unroll
-                for (int i = 0; i < r2; ++i) x[i] = replace_magnitude<kRes>(x[i], yv[u][i], inv_n, acc_d, acc_y);
+                replace_magnitudes<kRes>(x, yv[u], inv_n, acc_d, acc_y);
                 Dft<r2, true>::run(x);
 #pragma unroll
                 for (int i = 0; i < r2; ++i) sB[xcol(m * r2 + i, c)] = x[i];
@@ -465,7 +474,8 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
         __syncthreads();
         // ---- inverse first column stage (DIT, span N)
 #pragma unroll 1
-        for (int id = threadIdx.x; id < G::NB1; id += T) {
+        for (int it = 0; it < G::NB1 / T; ++it) {
+            const int id = threadIdx.x + it * T;
             const int c = id % 16, b = id / 16;
             float2 x[r1];
 #pragma unroll
@@ -490,7 +500,8 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
 
         // ---- inverse second row stage (span r2)
 #pragma unroll 1
-        for (int id = threadIdx.x; id < G::NB2; id += T) {
+        for (int it = 0; it < G::NB2 / T; ++it) {
+            const int id = threadIdx.x + it * T;
             const int k = id % 16, m = id / 16;
             float2 x[r2];
 #pragma unroll
@@ -500,62 +511,75 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
             for (int i = 0; i < r2; ++i) sA[xrow(k, m * r2 + i)] = x[i];
         }
         if (__syncthreads_or(!got_a)) break;
-        // ---- inverse first row stage fused with S4 + S5
+        // ---- inverse first row stage fused with S4 + S5 (the consensus
+        // loads and the residual sums only on the residual iteration)
         float acc_z = 0.f, acc_w = 0.f;
+        auto update = [&](auto with_res) {
+            constexpr bool kRes = decltype(with_res)::value;
 #pragma unroll 1
-        for (int id = threadIdx.x; id < G::NB1; id += T) {
-            int k, b;
-            row_butterfly(id, S1, k, b);
-            const int row = row0 + k;
-            float2 x[r1];
+            for (int it = 0; it < G::NB1 / T; ++it) {
+                const int id = threadIdx.x + it * T;
+                int k, b;
+                row_butterfly(id, S1, k, b);
+                const int row = row0 + k;
+                float2 x[r1];
 #pragma unroll
-            for (int t = 0; t < r1; ++t) x[t] = sA[xrow(k, b + S1 * t)];
+                for (int t = 0; t < r1; ++t) x[t] = sA[xrow(k, b + S1 * t)];
 #pragma unroll
-            for (int t = 1; t < r1; ++t) x[t] = cmulc(x[t], tw[t * S1 + b]);
-            Dft<r1, true>::run(x);
-            float2* qr = a.q + wbase + (size_t)row * N;   // read (S0) and overwritten (S5) by this thread only
-            float2* __restrict__ ur = a.u + wbase + (size_t)row * N;
-            const float2* __restrict__ dr = a.dinv + (size_t)row * N;
-            const float2* __restrict__ xr = a.xbar + (size_t)(off.x + row) * a.n2 + off.y;
-            // in quarters: the loads of a quarter are issued together
-            constexpr int H = r1 / 4;
-            if constexpr (kTm) tmem_wait_st();   // v of the copy-in has landed
+                for (int t = 1; t < r1; ++t) x[t] = cmulc(x[t], tw[t * S1 + b]);
+                Dft<r1, true>::run(x);
+                float2* qr = a.q + wbase + (size_t)row * N;   // read (S0) and overwritten (S5) by this thread only
+                float2* __restrict__ ur = a.u + wbase + (size_t)row * N;
+                const float2* __restrict__ xr = a.xbar + (size_t)(off.x + row) * a.n2 + off.y;
+                // in quarters: the loads of a quarter are issued together
+                constexpr int H = r1 / 4;
+                if constexpr (kTm) tmem_wait_st();   // v of the copy-in has landed
 #pragma unroll
-            for (int h0 = 0; h0 < r1; h0 += H) {
-                float2 qv[H], xv[H], dv[H];
-                if constexpr (kTm) {
-                    // v and 1/d from TMEM; the consensus values only feed the residual
-                    static_assert(H == 4, "one 8-column TMEM load per quarter and table");
-                    uint32_t rv[8], rd[8];
-                    tmem_ld8x2(tm_addr + 32u + 2u * (uint32_t)h0, rv, tm_addr + 2u * (uint32_t)h0, rd);
+                for (int h0 = 0; h0 < r1; h0 += H) {
+                    float2 qv[H], xv[H], dv[H];
+                    if constexpr (kTm) {
+                        // v and 1/d from TMEM; the consensus values only feed the residual
+                        static_assert(H == 4, "one 8-column TMEM load per quarter and table");
+                        uint32_t rv[8], rd[8];
+                        tmem_ld8x2(tm_addr + 32u + 2u * (uint32_t)h0, rv, tm_addr + 2u * (uint32_t)h0, rd);
 #pragma unroll
-                    for (int t = 0; t < H; ++t) {
-                        qv[t] = make_float2(__uint_as_float(rv[2 * t]), __uint_as_float(rv[2 * t + 1]));
-                        dv[t] = make_float2(__uint_as_float(rd[2 * t]), __uint_as_float(rd[2 * t + 1]));
-                        if (res) xv[t] = __ldg(xr + b + S1 * (h0 + t));
+                        for (int t = 0; t < H; ++t) {
+                            qv[t] = make_float2(__uint_as_float(rv[2 * t]), __uint_as_float(rv[2 * t + 1]));
+                            dv[t] = make_float2(__uint_as_float(rd[2 * t]), __uint_as_float(rd[2 * t + 1]));
+                            if constexpr (kRes) xv[t] = __ldg(xr + b + S1 * (h0 + t));
+                        }
+                    } else {
+                        const float2* __restrict__ dr = a.dinv + (size_t)row * N;
+#pragma unroll
+                        for (int t = 0; t < H; ++t) {
+                            const int s = b + S1 * (h0 + t);
+                            qv[t] = qr[s];
+                            xv[t] = __ldg(xr + s);
+                            dv[t] = __ldg(dr + s);
+                        }
                     }
-                } else {
+                    auto pixels = [&](auto check) {
+                        constexpr bool kCheck = decltype(check)::value;
 #pragma unroll
-                    for (int t = 0; t < H; ++t) {
-                        const int s = b + S1 * (h0 + t);
-                        qv[t] = qr[s];
-                        xv[t] = __ldg(xr + s);
-                        dv[t] = __ldg(dr + s);
-                    }
-                }
-#pragma unroll
-                for (int t = 0; t < H; ++t) {
-                    const int s = b + S1 * (h0 + t);
-                    float2 u, qn;
-                    // v: kept from the copy-in (TMEM), else q + 2 rho_prev xbar again
-                    const float2 v = kTm ? qv[t] : mann_close(qv[t], xv[t], two_rho_prev);
-                    const float2 w = agent_step(x[h0 + t], v, dv[t], scale, alpha, inv1pa, two_rho, u, qn);
-                    if (res) residual_sums(first ? v : xv[t], w, acc_z, acc_w);
-                    st_l2_hint(ur + s, u, pol_u);       // read by the consensus gather next
-                    st_l2_hint(qr + s, qn, pol_first);  // read again only next iteration
+                        for (int t = 0; t < H; ++t) {
+                            const int s = b + S1 * (h0 + t);
+                            float2 u, qn;
+                            // v: kept from the copy-in (TMEM), else q + 2 rho_prev xbar again
+                            const float2 v = kTm ? qv[t] : mann_close2(qv[t], xv[t], trp2);
+                            const float2 w =
+                                agent_step2<kCheck>(x[h0 + t], v, dv[t], scale2, alpha2, inv1pa2, m2rho2, u, qn);
+                            if constexpr (kRes) residual_sums(first ? v : xv[t], w, acc_z, acc_w);
+                            st_l2_hint(ur + s, u, pol_u);       // read by the consensus gather next
+                            st_l2_hint(qr + s, qn, pol_first);  // read again only next iteration
+                        }
+                    };
+                    if (absent) pixels(std::true_type{});
+                    else pixels(std::false_type{});
                 }
             }
-        }
+        };
+        if (res) update(std::true_type{});
+        else update(std::false_type{});
         // No barrier is needed before the next window: its copy-in writes
         // exactly the A rows this thread's warp has just read (the same
         // (k, b) butterflies), and the reduction buffer is only used here.
