@@ -534,7 +534,7 @@ __device__ __forceinline__ void pair_body(const AgentArgs& a, const int j0, cons
         const bool got_b = mbar_wait_bounded(bar_b, parity, a.err);
         // re-arm for the next pair before this CTA's next send: every peer's
         // next A -> B copy comes after it has received that send
-        if (threadIdx.x == 0 && j + 2 < jn) mbar_arrive_expect_tx(bar_b, kBytes);
+        if (threadIdx.x == 0 && got_b && j + 2 < jn) mbar_arrive_expect_tx(bar_b, kBytes);
 
         // ---- first DIF column stage (span N, radix 16)
         {
@@ -611,7 +611,7 @@ __device__ __forceinline__ void pair_body(const AgentArgs& a, const int j0, cons
                               cluster_addr(bar_a, p));
         }
         const bool got_a = mbar_wait_bounded(bar_a, parity, a.err);
-        if (threadIdx.x == 0 && j + 2 < jn) mbar_arrive_expect_tx(bar_a, kBytes);
+        if (threadIdx.x == 0 && got_a && j + 2 < jn) mbar_arrive_expect_tx(bar_a, kBytes);
 
         // ---- inverse second row stage (span r2)
 #pragma unroll

@@ -66,7 +66,12 @@ struct XposeGeom {
     static constexpr int S1 = N / r1;               // stride of the first stage (= r2)
     static constexpr int NB1 = R * S1;              // first-stage butterflies per slab
     static constexpr int NB2 = R * r1;              // second-stage butterflies per slab
-    static constexpr int kSmem = 2 * kSlab * (int)sizeof(float2) + N * (int)sizeof(float2) + 32;
+    // first-stage twiddles: one row of r1 values per butterfly, padded to
+    // kTwP elements (16-byte aligned rows; the 16-byte loads of the S1 rows
+    // fall in distinct banks)
+    static constexpr int kTwP = r1 + 2;
+    static constexpr int kTwElems = S1 * kTwP;
+    static constexpr int kSmem = 2 * kSlab * (int)sizeof(float2) + kTwElems * (int)sizeof(float2) + 32;
     // resident CTAs per SM: shared memory (228 KB, 1 KB reserved per CTA plus
     // the static reduction buffer), threads, and at least kRegFloor
     // registers a thread.  For 128 x 128 windows 96 registers (5 CTAs) keep
@@ -90,6 +95,8 @@ struct XposeGeom {
     static_assert(C >= 2 && C <= 16, "one block per CTA of the cluster");
     static_assert(kBlkBytes % 16 == 0, "bulk copies move multiples of 16 bytes between 16-byte aligned blocks");
     static_assert(S1 * r1 == N, "one twiddle table entry per (stage output, butterfly)");
+    static_assert(S1 <= 16 && 16 % r2 == 0, "stage offsets split into a base and a constant");
+    static_assert(r1 % 2 == 0 && kTwP % 2 == 0, "twiddles are read in 16-byte pairs from 16-byte aligned rows");
 };
 
 // First-stage butterfly of a row stage handled by thread slot id (0 ..
@@ -110,6 +117,33 @@ __device__ __forceinline__ int xslab(int blk, int k, int c) { return blk * 272 +
 __device__ __forceinline__ int xrow(int k, int s) { return xslab(s >> 4, k, s & 15); }
 // Column slab: storage row g, column c of the CTA.
 __device__ __forceinline__ int xcol(int g, int c) { return xslab(g >> 4, g & 15, c); }
+
+// The same offsets split into a per-thread base and a part that depends
+// only on the unrolled loop index, a compile-time constant, so that every
+// access of a stage is the base register plus an immediate.
+// First stages, element b + S1 t (b < S1 <= 16): block and position of t.
+template <int S1>
+__device__ __forceinline__ constexpr int x1_blk(int t) { return S1 >= 16 ? t * (S1 / 16) : t / (16 / S1); }
+template <int S1>
+__device__ __forceinline__ constexpr int x1_pos(int t) { return S1 >= 16 ? 0 : S1 * (t % (16 / S1)); }
+// xrow(k, b + S1 t) = xrow1_base(k, b) + xrow1_off<S1>(t)
+__device__ __forceinline__ int xrow1_base(int k, int b) { return k * 17 + b; }
+template <int S1>
+__device__ __forceinline__ constexpr int xrow1_off(int t) { return x1_blk<S1>(t) * 272 + x1_pos<S1>(t); }
+// xcol(b + S1 t, c) = xcol1_base(b, c) + xcol1_off<S1>(t)
+__device__ __forceinline__ int xcol1_base(int b, int c) { return b * 17 + c; }
+template <int S1>
+__device__ __forceinline__ constexpr int xcol1_off(int t) { return x1_blk<S1>(t) * 272 + x1_pos<S1>(t) * 17; }
+// Second stages, element m R2 + i (i < R2 <= 16):
+// xrow(k, m R2 + i) = xrow2_base<R2>(k, m) + i, xcol(m R2 + i, c) = xcol2_base<R2>(m, c) + 17 i
+template <int R2>
+__device__ __forceinline__ int xrow2_base(int k, int m) {
+    return (m / (16 / R2)) * 272 + k * 17 + R2 * (m % (16 / R2));
+}
+template <int R2>
+__device__ __forceinline__ int xcol2_base(int m, int c) {
+    return (m / (16 / R2)) * 272 + R2 * (m % (16 / R2)) * 17 + c;
+}
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
@@ -195,6 +229,19 @@ __device__ __forceinline__ void load_amps16(const void* y, size_t base, uint64_t
     }
 }
 
+// x[t] *= W^(b t) (CONJ: its conjugate) for t = 1 .. R - 1, from the
+// butterfly's row of the twiddle table, two values per 16-byte load.
+template <int R, bool CONJ>
+__device__ __forceinline__ void twiddle_row(float2 (&x)[R], const float2* row) {
+    const float4* w4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+    for (int p = 0; p < R / 2; ++p) {
+        const float4 w = w4[p];
+        if (p > 0) x[2 * p] = CONJ ? cmulc(x[2 * p], make_float2(w.x, w.y)) : cmul(x[2 * p], make_float2(w.x, w.y));
+        x[2 * p + 1] = CONJ ? cmulc(x[2 * p + 1], make_float2(w.z, w.w)) : cmul(x[2 * p + 1], make_float2(w.z, w.w));
+    }
+}
+
 // Windows j0 .. jn - 1 of the job `a` on one cluster.  TMC: keep 1/d and v
 // in TMEM where the geometry allows (the launched kernels); the twin
 // without it only serves the occupancy query (see agent_xpose).
@@ -209,7 +256,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
     float2* sA = reinterpret_cast<float2*>(smem_raw);
     float2* sB = sA + G::kSlab;
     float2* tw = sB + G::kSlab;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(tw + N);   // [0]: B slab filled, [1]: A slab filled, [2]: run done
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tw + G::kTwElems);   // [0]: B slab filled, [1]: A slab filled, [2]: run done
     __shared__ double red[(T / 32) * 4];
 
     cg::cluster_group cl = cg::this_cluster();
@@ -224,10 +271,9 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
         mbar_arrive_expect_tx(bar_b, kBytes);
         mbar_arrive_expect_tx(bar_a, kBytes);
     }
-    // twiddles of the first-stage butterflies, by stage output t then
-    // butterfly b: tw[t S1 + b] = W_N^(b t), so that the threads of a row
-    // stage read consecutive entries for each t
-    for (int i = threadIdx.x; i < N; i += T) tw[i] = a.tw[(i % S1) * (i / S1)];
+    // twiddles of the first-stage butterflies, by butterfly b then stage
+    // output t: tw[b kTwP + t] = W_N^(b t)
+    for (int i = threadIdx.x; i < N; i += T) tw[(i / r1) * G::kTwP + i % r1] = a.tw[(i / r1) * (i % r1)];
     cl.sync();   // every CTA's barriers are armed before any copy or arrival can land
 
     const float two_rho_prev = 2.0f * a.rho_prev;
@@ -385,10 +431,9 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
                 for (int t = 0; t < r1; ++t) x[t] = cmul(__ldg(dr + b + S1 * t), x[t]);
             }
             Dft<r1, false>::run(x);
+            twiddle_row<r1, false>(x, tw + b * G::kTwP);
 #pragma unroll
-            for (int t = 1; t < r1; ++t) x[t] = cmul(x[t], tw[t * S1 + b]);
-#pragma unroll
-            for (int t = 0; t < r1; ++t) sA[xrow(k, b + S1 * t)] = x[t];
+            for (int t = 0; t < r1; ++t) sA[xrow1_base(k, b) + xrow1_off<S1>(t)] = x[t];
         }
         __syncthreads();
         // ---- second DIF row stage (span r2)
@@ -398,10 +443,10 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
             const int k = id % 16, m = id / 16;
             float2 x[r2];
 #pragma unroll
-            for (int i = 0; i < r2; ++i) x[i] = sA[xrow(k, m * r2 + i)];
+            for (int i = 0; i < r2; ++i) x[i] = sA[xrow2_base<r2>(k, m) + i];
             Dft<r2, false>::run(x);
 #pragma unroll
-            for (int i = 0; i < r2; ++i) sA[xrow(k, m * r2 + i)] = x[i];
+            for (int i = 0; i < r2; ++i) sA[xrow2_base<r2>(k, m) + i] = x[i];
         }
         fence_proxy_async_smem();
         __syncthreads();
@@ -427,8 +472,11 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
         }
         const bool got_b = mbar_wait_bounded(bar_b, parity, a.err);
         // re-arm for the next window before this CTA's next send: every
-        // peer's next A -> B copy comes after it has received that send
-        if (threadIdx.x == 0 && j + 1 < jn) mbar_arrive_expect_tx(bar_b, kBytes);
+        // peer's next A -> B copy comes after it has received that send.
+        // Only after a completed phase: a wait that gave up leaves the
+        // barrier as it is (its phase still counts the missing bytes), and
+        // the CTA stops at the next block barrier.
+        if (threadIdx.x == 0 && got_b && j + 1 < jn) mbar_arrive_expect_tx(bar_b, kBytes);
 
         // ---- first DIF column stage (span N, radix r1)
 #pragma unroll 1
@@ -437,12 +485,11 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
             const int c = id % 16, b = id / 16;
             float2 x[r1];
 #pragma unroll
-            for (int t = 0; t < r1; ++t) x[t] = sB[xcol(b + S1 * t, c)];
+            for (int t = 0; t < r1; ++t) x[t] = sB[xcol1_base(b, c) + xcol1_off<S1>(t)];
             Dft<r1, false>::run(x);
+            twiddle_row<r1, false>(x, tw + b * G::kTwP);
 #pragma unroll
-            for (int t = 1; t < r1; ++t) x[t] = cmul(x[t], tw[t * S1 + b]);
-#pragma unroll
-            for (int t = 0; t < r1; ++t) sB[xcol(b + S1 * t, c)] = x[t];
+            for (int t = 0; t < r1; ++t) sB[xcol1_base(b, c) + xcol1_off<S1>(t)] = x[t];
         }
         // a wait that gave up stops the CTA before it sends anything more
         if (__syncthreads_or(!got_b)) break;
@@ -457,7 +504,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
                 const int c = id % 16, m = id / 16;
                 float2 x[r2];
 #pragma unroll
-                for (int i = 0; i < r2; ++i) x[i] = sB[xcol(m * r2 + i, c)];
+                for (int i = 0; i < r2; ++i) x[i] = sB[xcol2_base<r2>(m, c) + 17 * i];
                 Dft<r2, false>::run(x);
                 if (a.spectrum) {   // check of the forward transform (kernel row m r2 + i, column row0 + c)
 #pragma unroll
@@ -466,7 +513,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
                 replace_magnitudes<kRes>(x, yv[u], inv_n, acc_d, acc_y);
                 Dft<r2, true>::run(x);
 #pragma unroll
-                for (int i = 0; i < r2; ++i) sB[xcol(m * r2 + i, c)] = x[i];
+                for (int i = 0; i < r2; ++i) sB[xcol2_base<r2>(m, c) + 17 * i] = x[i];
             }
         };
         if (res) column_step(std::true_type{});
@@ -479,12 +526,11 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
             const int c = id % 16, b = id / 16;
             float2 x[r1];
 #pragma unroll
-            for (int t = 0; t < r1; ++t) x[t] = sB[xcol(b + S1 * t, c)];
-#pragma unroll
-            for (int t = 1; t < r1; ++t) x[t] = cmulc(x[t], tw[t * S1 + b]);
+            for (int t = 0; t < r1; ++t) x[t] = sB[xcol1_base(b, c) + xcol1_off<S1>(t)];
+            twiddle_row<r1, true>(x, tw + b * G::kTwP);
             Dft<r1, true>::run(x);
 #pragma unroll
-            for (int t = 0; t < r1; ++t) sB[xcol(b + S1 * t, c)] = x[t];
+            for (int t = 0; t < r1; ++t) sB[xcol1_base(b, c) + xcol1_off<S1>(t)] = x[t];
         }
         fence_proxy_async_smem();
         __syncthreads();
@@ -496,7 +542,7 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
                               cluster_addr(bar_a, p));
         }
         const bool got_a = mbar_wait_bounded(bar_a, parity, a.err);
-        if (threadIdx.x == 0 && j + 1 < jn) mbar_arrive_expect_tx(bar_a, kBytes);
+        if (threadIdx.x == 0 && got_a && j + 1 < jn) mbar_arrive_expect_tx(bar_a, kBytes);
 
         // ---- inverse second row stage (span r2)
 #pragma unroll 1
@@ -505,10 +551,10 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
             const int k = id % 16, m = id / 16;
             float2 x[r2];
 #pragma unroll
-            for (int i = 0; i < r2; ++i) x[i] = sA[xrow(k, m * r2 + i)];
+            for (int i = 0; i < r2; ++i) x[i] = sA[xrow2_base<r2>(k, m) + i];
             Dft<r2, true>::run(x);
 #pragma unroll
-            for (int i = 0; i < r2; ++i) sA[xrow(k, m * r2 + i)] = x[i];
+            for (int i = 0; i < r2; ++i) sA[xrow2_base<r2>(k, m) + i] = x[i];
         }
         if (__syncthreads_or(!got_a)) break;
         // ---- inverse first row stage fused with S4 + S5 (the consensus
@@ -524,9 +570,8 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
                 const int row = row0 + k;
                 float2 x[r1];
 #pragma unroll
-                for (int t = 0; t < r1; ++t) x[t] = sA[xrow(k, b + S1 * t)];
-#pragma unroll
-                for (int t = 1; t < r1; ++t) x[t] = cmulc(x[t], tw[t * S1 + b]);
+                for (int t = 0; t < r1; ++t) x[t] = sA[xrow1_base(k, b) + xrow1_off<S1>(t)];
+                twiddle_row<r1, true>(x, tw + b * G::kTwP);
                 Dft<r1, true>::run(x);
                 float2* qr = a.q + wbase + (size_t)row * N;   // read (S0) and overwritten (S5) by this thread only
                 float2* __restrict__ ur = a.u + wbase + (size_t)row * N;
