@@ -45,7 +45,14 @@ rounding changes:
   in32_all32    the same inputs, and every step of Algorithm 1 in single
                 precision (complex64 transforms, agent arithmetic, consensus
                 sums and state, float32 weights), in the oracle's order: the
-                arithmetic precision the hot path is specified to use.
+                arithmetic precision the hot path is specified to use;
+  in32_ulpS     (bench-parameter curve only, S = 1 .. 6) the in32 inputs with
+                every amplitude and every real and imaginary part of the
+                probe moved by one single-precision unit of relative size
+                2^-24, up or down at random (seed S), then the plain FP64
+                oracle: an ensemble of equally sized rounding changes, which
+                samples how far rounding alone moves a curve that does not
+                converge.
 """
 import json
 import os
@@ -65,6 +72,7 @@ LIT_FRACTION = 0.1
 C30 = dict(n_obj=600, n_p=128, probe_sigma=32.0, n_scan=30, step=16, jitter=2, name="c30")
 
 PERTURBATIONS = ("in32", "in32_state32", "in32_fft32", "in32_all32")
+ULP_SEEDS = (1, 2, 3, 4, 5, 6)
 
 
 def _spec(group, workload, seed, iters, every, alpha, kappa, peak=None, perturbation=None, rho=0.5):
@@ -86,6 +94,7 @@ CURVES += [_spec("small", "small", 1, 50, 5, a, 1.25) for a in (0.5, 2.0)]
 # the rounding-sized perturbations of the bench-parameter curve and of the
 # alpha = 0.5 curves of the converging geometry
 SPREAD = [dict(CURVES[0], perturbation=p) for p in PERTURBATIONS]
+SPREAD += [dict(CURVES[0], perturbation=f"in32_ulp{k}") for k in ULP_SEEDS]
 SPREAD += [dict(c, perturbation=p) for c in CURVES if c["group"] == "c30" and c["alpha"] == 0.5
            for p in ("in32", "in32_all32")]
 
@@ -178,10 +187,17 @@ def curve(spec):
     cover, lit = masks(w, kappa)
     probe, y = w.probe, w.y
     if pert is not None:
-        if pert not in PERTURBATIONS:
+        ulp_seed = int(pert[len("in32_ulp"):]) if pert.startswith("in32_ulp") else None
+        if pert not in PERTURBATIONS and ulp_seed not in ULP_SEEDS:
             raise ValueError(pert)
         probe = w.probe.astype(np.complex64).astype(np.complex128)
         y = w.y.astype(np.float32).astype(np.float64)
+        if ulp_seed is not None:
+            rng = np.random.Generator(np.random.PCG64(1000 + ulp_seed))
+            eps = 2.0 ** -24
+            y = y * (1.0 + eps * rng.choice((-1.0, 1.0), size=y.shape))
+            probe = (probe.real * (1.0 + eps * rng.choice((-1.0, 1.0), size=probe.shape))
+                     + 1j * probe.imag * (1.0 + eps * rng.choice((-1.0, 1.0), size=probe.shape)))
     if pert == "in32_fft32":   # this process only (one spawned process per curve)
         orc.fft2o, orc.ifft2o = _fft2o_32, _ifft2o_32
     state32 = pert == "in32_state32"

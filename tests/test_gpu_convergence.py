@@ -12,16 +12,18 @@ the oracle's curve:
   workload on a 30 x 30 scan, Poisson peaks 1e4 and 1e6, alpha 0.5 and 2)
   and the 169-window workload: within 1 % at every stored count, on both
   masks (the analogue of the paper's NRMSE-against-iteration figures);
-* the 600 x 600 / 256 x 256 / 324-window workload at the bench's parameters:
-  on the well-illuminated mask within max(1 %, twice the largest move of a
-  rounding-perturbed oracle run) at every stored count; on the covered mask
-  at the first and the final count.  Its edge pixels see the probe at 1e-2
-  to 1e-3 of its peak, 1/d amplifies their data term by as much, and the
+* the 600 x 600 / 256 x 256 / 324-window workload at the bench's parameters,
+  at every stored count: on the well-illuminated mask within 1 %; on the
+  covered mask within max(1 %, twice the largest move of a
+  rounding-perturbed oracle run).  Its edge pixels see the probe at 1e-2 to
+  1e-3 of its peak, 1/d amplifies their data term by as much, and the
   covered-mask error (about 1.6, above that of a zero image) is set by
-  pixels the data do not determine: runs that differ only in rounding move
-  it by up to 3 % from one count to the next.  The accuracy of each step
-  there is checked directly instead (one step from the oracle's state
-  against the same step computed wholly in single precision);
+  pixels the data do not determine: runs whose inputs differ by one
+  single-precision unit move it by 0.7 % after 10 iterations, 1.6 % after
+  20 and up to 5.6 % later, so the perturbed runs include an ensemble of six
+  such input changes.  The accuracy of each step is also checked directly
+  (one step from the oracle's state against the same step computed wholly
+  in single precision);
 * the alpha / kappa sweep on that workload: 5 % on the final error and the
   grid's ranking.
 """
@@ -110,14 +112,18 @@ def test_golden_curves_are_the_configured_runs():
 def test_oracle_spread_is_rounding_sized():
     """Where the plain 1 % bar is used, rounding alone moves the oracle's
     curve by less than half of it: every count of the converging geometry on
-    both masks, the first count of the bench-parameter curve."""
+    both masks, the first count of the bench-parameter curve on the
+    well-illuminated mask.  On the covered mask of the bench-parameter curve
+    the perturbed runs stay below the 1 % bar itself at the first count and
+    spread further as the run goes on (the curve does not converge)."""
     for spec in GEN.CURVES:
         if spec["group"] == "c30" and spec["alpha"] == 0.5:
             for key in ("nrmse", "nrmse_lit"):
                 assert max(spread(spec, key)) <= TIGHT_SPREAD, (GEN.out_name(spec), key)
     p256 = GEN.CURVES[0]
-    assert spread(p256, "nrmse")[0] <= TIGHT_SPREAD
     assert spread(p256, "nrmse_lit")[0] <= TIGHT_SPREAD
+    assert spread(p256, "nrmse")[0] <= TOL_NRMSE_REL
+    assert len([sp for sp in GEN.SPREAD if dict(sp, perturbation=None) == dict(p256, perturbation=None)]) == 10
 
 
 def test_converging_oracle_curves_fall_below_a_tenth():
@@ -177,13 +183,12 @@ def test_p256_nrmse_at_bench_parameters(p256_curves):
     assert (spec["alpha"], spec["kappa"]) == (0.5, 1.25)
     ref = [p["nrmse"] for p in g["points"]]
     ref_lit = [p["nrmse_lit"] for p in g["points"]]
-    sp, sp_lit = spread(spec, "nrmse"), spread(spec, "nrmse_lit")
+    sp = spread(spec, "nrmse")
     for i, (e, e_lit) in enumerate(got):
-        bar = max(TOL_NRMSE_REL, 2.0 * sp_lit[i])
-        assert abs(e_lit - ref_lit[i]) <= bar * ref_lit[i], (g["points"][i]["iteration"], e_lit, ref_lit[i], bar)
-    for i in (0, len(ref) - 1):
+        it = g["points"][i]["iteration"]
+        assert abs(e_lit - ref_lit[i]) <= TOL_NRMSE_REL * ref_lit[i], (it, e_lit, ref_lit[i])
         bar = max(TOL_NRMSE_REL, 2.0 * sp[i])
-        assert abs(got[i][0] - ref[i]) <= bar * ref[i], (g["points"][i]["iteration"], got[i][0], ref[i], bar)
+        assert abs(e - ref[i]) <= bar * ref[i], (it, e, ref[i], bar)
     assert (got[-1][0] < got[0][0]) == (ref[-1] < ref[0])
 
 
