@@ -185,9 +185,12 @@ std::vector<int> amp_layout(int np, int variant, int elem) {
 
 // Windows each agent cluster processes: the variant's own count, or for the
 // transposing exchange (a run of windows per cluster) J spread over four
-// times the clusters the device holds at once, and at most 8: short runs let
-// the clusters that finish early take up the remaining ones, which balances
-// SMs that hold different numbers of CTAs (PMACE_AGENT_WPC fixes the run).
+// times the clusters the device holds at once, and at most 16: runs short
+// enough that the clusters that finish early take up the remaining ones,
+// which balances SMs that hold different numbers of CTAs, and long enough
+// to amortise a cluster's start (TMEM and twiddle tables, the cluster
+// barrier); on the 64009-window scan runs of 4, 8, 16 and 32 windows took
+// 8.27, 8.03, 7.93 and 7.92 ms (PMACE_AGENT_WPC fixes the run).
 // The packed-lane sweep counts in pairs of windows, so its runs are even.
 int windows_per_cluster(int np, int variant, int J, const AgentPlanInfo& info) {
     const AgentVariant v = agent_variant_of(np, variant);
@@ -198,7 +201,7 @@ int windows_per_cluster(int np, int variant, int J, const AgentPlanInfo& info) {
         if (w > 0) return (w + unit - 1) / unit * unit;
     }
     const int m = 4 * std::max(info.max_clusters, 1) * unit;
-    return unit * std::max(1, std::min(8 / unit, (J + m - 1) / m));
+    return unit * std::max(1, std::min(16 / unit, (J + m - 1) / m));
 }
 
 // Gather tables of one tile height: for every tile_h x kGatherTileW image
