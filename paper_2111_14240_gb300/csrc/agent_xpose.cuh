@@ -436,7 +436,14 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
             for (int t = 0; t < r1; ++t) sA[xrow1_base(k, b) + xrow1_off<S1>(t)] = x[t];
         }
         __syncthreads();
-        // ---- second DIF row stage (span r2)
+        // ---- second DIF row stage (span r2), and A -> B.  Block `rank` of
+        // peer p's B was last read by p's own copy of it back to this CTA in
+        // the previous window, which landed before this CTA passed its wait
+        // on the A slab: p's region is free.  A warp's butterflies of one
+        // iteration cover all 16 rows of 2 r2 whole columns; where that is a
+        // whole number of blocks (r2 >= 8), the warp sends them itself as
+        // soon as it has written them, without a block barrier.
+        constexpr bool kWarpSends = (2 * r2) % 16 == 0;
 #pragma unroll 1
         for (int it = 0; it < G::NB2 / T; ++it) {
             const int id = threadIdx.x + it * T;
@@ -447,16 +454,25 @@ __device__ __forceinline__ void xpose_body(const AgentArgs& a, const int j0, con
             Dft<r2, false>::run(x);
 #pragma unroll
             for (int i = 0; i < r2; ++i) sA[xrow2_base<r2>(k, m) + i] = x[i];
+            if constexpr (kWarpSends) {
+                constexpr int kBlocksPerWarp = 2 * r2 / 16;
+                fence_proxy_async_smem();
+                __syncwarp();
+                const int lane = threadIdx.x & 31;
+                const int p = ((id & ~31) / 16) * r2 / 16 + lane;   // first column of the warp / 16, + lane
+                if (lane < kBlocksPerWarp)
+                    bulk_copy_to_peer(cluster_addr(b_base + (uint32_t)rank * kBlkBytes, (uint32_t)p),
+                                      a_base + (uint32_t)p * kBlkBytes, kBlkBytes, cluster_addr(bar_b, (uint32_t)p));
+            }
         }
-        fence_proxy_async_smem();
-        __syncthreads();
-        // ---- A -> B.  Block `rank` of peer p's B was last read by p's own
-        // copy of it back to this CTA in the previous window, which landed
-        // before this CTA passed its wait on the A slab: p's region is free.
-        if (threadIdx.x < C) {
-            const uint32_t p = threadIdx.x;
-            bulk_copy_to_peer(cluster_addr(b_base + (uint32_t)rank * kBlkBytes, p), a_base + p * kBlkBytes, kBlkBytes,
-                              cluster_addr(bar_b, p));
+        if constexpr (!kWarpSends) {
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (threadIdx.x < C) {
+                const uint32_t p = threadIdx.x;
+                bulk_copy_to_peer(cluster_addr(b_base + (uint32_t)rank * kBlkBytes, p), a_base + p * kBlkBytes,
+                                  kBlkBytes, cluster_addr(bar_b, p));
+            }
         }
         // amplitudes of this thread's column butterflies (value u r2 + i of
         // the thread order is element i of butterfly u), loaded while the
