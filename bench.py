@@ -486,6 +486,42 @@ def roofline_of(kt, J, np_, amp_bytes, workload):
             "algorithmic_bytes_per_window": agent_bytes_per_patch(np_, amp_bytes), "avg_launch_ms": agent_avg_ms}
 
 
+def agent_flops_per_window(np_: int) -> int:
+    """Nominal FP32 operations of one window's agent update: 10 P log2 P for
+    the forward and inverse 2-D transforms and about 45 P for the probe
+    products, the magnitude replacement and the update (P = Np^2)."""
+    P = np_ * np_
+    return int(10 * P * math.log2(P) + 45 * P)
+
+
+def fp32_peak_tflops() -> float:
+    """FP32 (CUDA-core) throughput of the device: a float32 matrix product
+    of 8192^3 with TF32 off, best of 5 (CUDA events)."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        n = 8192
+        g = torch.Generator(device="cuda").manual_seed(0)
+        a = torch.randn(n, n, device="cuda", generator=g)
+        b = torch.randn(n, n, device="cuda", generator=g)
+        for _ in range(2):
+            c = a @ b
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = float("inf")
+        for _ in range(5):
+            e0.record()
+            c = a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b, c
+        torch.cuda.empty_cache()
+        return 2.0 * n ** 3 / (best / 1e3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 def extra_workload(name: str, steps: int, warmup: int, stream):
     """Throughput and agent roofline of another workload (device-resident
     inputs), for the record beside the headline."""
@@ -604,6 +640,14 @@ def run_ours(args):
                         "iterations + residual + image readback; bytes amortised over K"},
         "host": host_info(),
     }
+    if world == 1:
+        fp = fp32_peak_tflops()
+        fl = agent_flops_per_window(np_)
+        ach = J * fl / (roof["avg_launch_ms"] / 1e3) / 1e12
+        line["kernels"]["agent_fp32"] = {
+            "flops_per_window": fl, "achieved_tflops": ach, "peak_tflops": fp, "frac": ach / fp,
+            "peak_kind": "measured float32 matrix product, TF32 off (CUDA cores), best of 5",
+            "note": "nominal FFT and update operations (10 P log2 P + 45 P, P = Np^2) per launch / average launch time"}
     if world == 1 and not args.no_extra:
         line["extra"] = {}
         for other in ("p256", "p128", "p128_f32"):
