@@ -89,7 +89,7 @@ cudaError_t agent_entry(int np, const AgentArgs* a, int variant, int amp, cudaSt
 // agent_variant_of) when set and valid, else PMACE_AGENT_CLUSTER selects the
 // first variant with that cluster size, else the probe size's default
 // (default_agent_variant).
-int default_variant(int np) {
+int default_variant(int np, int J) {
     if (const char* env = std::getenv("PMACE_AGENT_PLAN")) {
         const int v = std::atoi(env);
         if (v >= 0 && v < kAgentVariants) return v;
@@ -99,7 +99,7 @@ int default_variant(int np) {
         for (int v = 0; v < kAgentVariants; ++v)
             if (agent_variant_of(np, v).cluster == c) return v;
     }
-    return default_agent_variant(np);
+    return default_agent_variant(np, J);
 }
 
 // Row order of the amplitudes for a cluster size: kernel row g holds
@@ -714,7 +714,7 @@ pmace_status pmace_create(const pmace_dims* dims, const float* probe, const int3
 
     // plan: the requested variant if the device can run it, else the first that it can
     {
-        const int v0 = default_variant(np);
+        const int v0 = default_variant(np, J);
         int chosen = -1;
         for (int i = 0; i < kAgentVariants && chosen < 0; ++i) {
             const int v = (v0 + i) % kAgentVariants;

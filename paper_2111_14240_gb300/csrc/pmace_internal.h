@@ -121,11 +121,16 @@ __host__ __device__ constexpr AgentVariant agent_variant_of(int np, int v) {
         {16, 2, 0, 1, 0}, {16, 2, 0, 2, 0}, {8, 1, 1, 1, 0}, {8, 2, 0, 1, 0}, {16, 1, 0, 1, 1}, {16, 1, 0, 2, 2}};
     return np == 32 ? t32[v] : np == 64 ? t64[v] : np == 128 ? t128[v] : t256[v];
 }
-// The fastest variant measured on GB300 for each probe size: the in-place
-// cross-CTA stage for 32 x 32 probes (variant 0) and for 64 x 64 probes
-// (variant 2: two CTAs per window, amplitudes staged in shared memory), the
-// transposing exchange (variant 4) for 128 x 128 and 256 x 256.
-__host__ __device__ constexpr int default_agent_variant(int np) { return np >= 128 ? 4 : np == 64 ? 2 : 0; }
+// The fastest variant measured on GB300 for each probe size and J windows:
+// the transposing exchange (variant 4) for 64 x 64 and larger probes (on a
+// 1024^2 / 3600-window scan 0.174 ms against 0.179 ms for the best in-place
+// variant); for 32 x 32 probes one CTA per window (variant 1) once J fills
+// the GPU (0.042 ms against 0.066 ms on a 512^2 / 3600-window scan), else
+// two CTAs per window (variant 0: 0.0121 ms against 0.0140 ms for 169
+// windows).
+__host__ __device__ constexpr int default_agent_variant(int np, int J) {
+    return np >= 64 ? 4 : J >= 1024 ? 1 : 0;
+}
 
 // Geometry of one agent plan (probe size, CTAs per patch).
 struct AgentPlanInfo {
