@@ -20,7 +20,9 @@
 //   rows   copy-in fused with the first (span Np) DIF row stage, in
 //          registers; second row stage in A;
 //   A -> B bulk copies (cp.async.bulk shared::cta -> shared::cluster), each
-//          counted on the receiving CTA's mbarrier;
+//          counted on the receiving CTA's mbarrier; where a warp's
+//          second-stage butterflies cover whole blocks (Np >= 64) the warp
+//          sends them as soon as it has written them;
 //   cols   first DIF column stage in B; second column stage, magnitude
 //          replacement (S3) and the inverse second stage in registers;
 //          inverse first column stage in B;
